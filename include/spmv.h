@@ -1,0 +1,212 @@
+/*
+ * spmv.h -- C ABI of the GB300 (sm_103a) SpMV engine.
+ *
+ * The operation is the sparse matrix-vector product of Section 2.2 of
+ * Auto-SpMV (arXiv 2302.05662), Y = A X, extended with the BLAS scalars:
+ *
+ *     y <- alpha * A * x + beta * y
+ *
+ * for a sparse m x n matrix A held on the GPU in one of the storage formats
+ * of Section 2.3 (CSR, ELL, and a blocked format -- here BSR, the row-block
+ * form of the paper's BELL) or in COO and HYB (ELL + COO), and the kernel
+ * and launch parameters of Section 4 (thread-block size, register cap,
+ * L1/shared-memory split) plus threads-per-row and unroll form the tuned
+ * space.  The matrix arrives as COO triplets, the form the paper's input
+ * collection ships in (Section 7.5), and is converted on the device.
+ *
+ * Conventions shared by every entry point
+ *   - Pointers named d_* are CUDA device pointers; h_* are host pointers.
+ *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream.  All device work is ordered on that stream.  Calls that must
+ *     learn a size on the host (create, set_config, features, select)
+ *     synchronise that stream once; spmv_run never synchronises.
+ *   - Every function returns an spmv_status (0 = success).  On failure
+ *     spmv_last_error() returns a message for the calling thread.  No C++
+ *     exception or process exit crosses this boundary.
+ *   - Value types: SPMV_F64 values use double x and y and accumulate in
+ *     double; SPMV_F32 and SPMV_BF16 values use float x and y and
+ *     accumulate in float.  Indices are int32 (m, n < 2^31, nnz < 2^31).
+ *   - A handle is not thread-safe; runs on one handle must be ordered on
+ *     one stream (they share the handle's reduction scratch).
+ */
+#ifndef SPMV_GB300_SPMV_H
+#define SPMV_GB300_SPMV_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SPMV_API __attribute__((visibility("default")))
+#else
+#define SPMV_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct spmv_matrix *spmv_handle;
+
+typedef enum {
+    SPMV_OK = 0,
+    SPMV_ERR_INVALID = -1,     /* bad argument or triplet out of range     */
+    SPMV_ERR_OOM = -2,         /* device allocation failed                 */
+    SPMV_ERR_CUDA = -3,        /* a CUDA runtime call failed               */
+    SPMV_ERR_UNSUPPORTED = -4, /* valid but not supported (e.g. ELL width) */
+    SPMV_ERR_BOUNDS = -5,      /* a device-side bounds check fired         */
+    SPMV_ERR_TIMEOUT = -6      /* a bounded device wait gave up            */
+} spmv_status;
+
+typedef enum { SPMV_F64 = 0, SPMV_F32 = 1, SPMV_BF16 = 2 } spmv_dtype;
+
+typedef enum {
+    SPMV_FMT_CSR = 0, /* Section 2.3: Data, Column Index, Row Index        */
+    SPMV_FMT_ELL = 1, /* Section 2.3: m x max_nnz padded, column-major     */
+    SPMV_FMT_COO = 2, /* (row, col, val) triplets sorted by row            */
+    SPMV_FMT_HYB = 3, /* ELL part + COO overflow                           */
+    SPMV_FMT_BSR = 4  /* r x r dense blocks (blocked format of Sec. 2.3)   */
+} spmv_format;
+
+/* threads_per_row value that selects the nnz-balanced CSR kernel. */
+#define SPMV_TPR_SPLIT (-1)
+
+/*
+ * Kernel and launch parameters (Section 4, items 1-3, plus the format of
+ * item 4).  A zero field takes the library default.
+ *   format            spmv_format.
+ *   threads_per_block 32..1024, a power of two (default 256).
+ *   threads_per_row   CSR: lanes cooperating on one row, 1/2/4/8/16/32, or
+ *                     SPMV_TPR_SPLIT for the nnz-balanced split (default:
+ *                     the power of two nearest a quarter of the mean row
+ *                     length, capped at 32).  BSR: blocks handled at once per block row,
+ *                     1/2/4/8 (default 1).  Ignored by ELL, COO and HYB.
+ *   unroll            1, 2 or 4 (default 2): loads in flight per lane (ELL,
+ *                     CSR) or items per lane / 4 (COO, HYB tail, split CSR).
+ *   regcap            register cap per thread: 64 (default; the ceiling
+ *                     that keeps 1024-thread blocks launchable) or 32
+ *                     (the paper's maxrregcount knob).
+ *   carveout          preferred shared-memory carveout in percent (0..100),
+ *                     or -1 to leave the driver default (Section 4 item 3).
+ *                     Zero means 0 % (maximum L1), not "default".
+ *   bsr_block         BSR block size r: 2 or 4 (default 4).
+ *   hyb_ell_width     HYB ELL width; 0 applies the width rule (the largest
+ *                     k such that at least max(4096, m/3) rows hold k or
+ *                     more nonzeros).
+ * spmv_config_default() fills the defaults (with carveout = -1).
+ */
+typedef struct {
+    int32_t format;
+    int32_t threads_per_block;
+    int32_t threads_per_row;
+    int32_t unroll;
+    int32_t regcap;
+    int32_t carveout;
+    int32_t bsr_block;
+    int32_t hyb_ell_width;
+} spmv_config;
+
+/* Sizes of a handle's matrix and of its active format. */
+typedef struct {
+    int64_t m, n;
+    int64_t nnz;          /* stored entries after merging duplicate pairs  */
+    int64_t max_row;      /* longest row                                   */
+    int64_t ell_width;    /* ELL width (ELL), or ELL-part width (HYB)      */
+    int64_t hyb_coo_nnz;  /* entries in the HYB COO part                   */
+    int64_t bsr_blocks;   /* nonzero r x r blocks (BSR)                    */
+    int64_t format_bytes; /* device bytes the active format's kernel reads */
+    int32_t value_type;   /* spmv_dtype                                    */
+    int32_t format;       /* active spmv_format                            */
+} spmv_info;
+
+/* Fills *cfg with the library defaults for `format` (carveout = -1). */
+SPMV_API void spmv_config_default(spmv_config *cfg, int32_t format);
+
+/*
+ * Build a matrix handle from COO triplets on the device (Section 5.3, step
+ * 4: conversion from the input COO to the chosen format; Section 7.5: the
+ * input is COO).  d_rows[k], d_cols[k], d_vals[k] (k < nnz) give entry
+ * (row, col, value); the triplets may come in any order and may repeat a
+ * (row, col) pair, whose values are then summed in triplet order.  Values
+ * are of `value_type` (double, float or bf16 bits).  The triplet arrays are
+ * borrowed for the duration of the call only; the handle owns copies in
+ * the converted format.  `cfg` (may be NULL = default CSR) selects the
+ * active format and kernel.  m, n may be 0; nnz may be 0.
+ * Errors: SPMV_ERR_INVALID for negative sizes, a NULL array with nnz > 0,
+ * or any triplet outside [0,m) x [0,n) (checked on the device);
+ * SPMV_ERR_UNSUPPORTED for m, n or nnz >= 2^31 or a format whose padded
+ * size exceeds the limit (ELL); SPMV_ERR_OOM; SPMV_ERR_CUDA.
+ * Synchronises `stream`.
+ */
+SPMV_API int spmv_create(spmv_handle *out, int64_t m, int64_t n, int64_t nnz,
+                const int32_t *d_rows, const int32_t *d_cols,
+                const void *d_vals, int32_t value_type,
+                const spmv_config *cfg, void *stream);
+
+/*
+ * Switch the active format and kernel parameters (Section 5.3 step 4, the
+ * re-pack once a better format is chosen; Section 5.2, the compile-time
+ * parameters, here pre-built kernel variants).  Packs the new format from
+ * the handle's CSR arrays on the device; frees the previous non-CSR arrays.
+ * Errors as for spmv_create.  Synchronises `stream`.
+ */
+SPMV_API int spmv_set_config(spmv_handle h, const spmv_config *cfg, void *stream);
+
+/* Copies the active (resolved, defaults filled) configuration. */
+SPMV_API int spmv_get_config(spmv_handle h, spmv_config *out);
+
+/* Copies the handle's sizes into *out. */
+SPMV_API int spmv_get_info(spmv_handle h, spmv_info *out);
+
+/*
+ * y <- alpha * A * x + beta * y (Section 2.2), using the active format.
+ * d_x holds n values and d_y m values, of type double (SPMV_F64) or float
+ * (SPMV_F32, SPMV_BF16); both are caller-owned device buffers, and x must
+ * not overlap y.  beta == 0 means y is not read (NaN in y is ignored).
+ * One or two kernel launches on `stream`; never synchronises.
+ * Errors: SPMV_ERR_INVALID for a NULL handle or a NULL vector with a
+ * nonzero size; SPMV_ERR_CUDA if a launch fails.
+ */
+SPMV_API int spmv_run(spmv_handle h, double alpha, const void *d_x, double beta,
+             void *d_y, void *stream);
+
+/* Array ids for spmv_export / spmv_export_bytes (test and debug access). */
+typedef enum {
+    SPMV_ARR_CSR_ROWPTR = 0,  /* int32[m+1]                                  */
+    SPMV_ARR_CSR_COLIDX = 1,  /* int32[nnz]                                  */
+    SPMV_ARR_CSR_VALS = 2,    /* value_type[nnz]                             */
+    SPMV_ARR_ELL_COLIDX = 3,  /* int32[width][pitch], -1 = padding           */
+    SPMV_ARR_ELL_VALS = 4,    /* value_type[width][pitch], 0 = padding       */
+    SPMV_ARR_COO_ROWS = 5,    /* int32[nnz] (COO) or int32[coo_nnz] (HYB)    */
+    SPMV_ARR_COO_COLS = 6,    /* int32[...] as above                         */
+    SPMV_ARR_COO_VALS = 7,    /* value_type[...] as above                    */
+    SPMV_ARR_BSR_ROWPTR = 8,  /* int32[ceil(m/r)+1]                          */
+    SPMV_ARR_BSR_COLIDX = 9,  /* int32[blocks]: block column                 */
+    SPMV_ARR_BSR_VALS = 10,   /* value_type[blocks][r][r], row-major blocks  */
+    SPMV_ARR_ELL_PITCH = 11   /* (size query only) pitch in elements          */
+} spmv_array_id;
+
+/*
+ * Size in bytes of an internal array of the active format (0 if the format
+ * does not hold it).  For SPMV_ARR_ELL_PITCH, *bytes receives the pitch in
+ * elements instead.
+ */
+SPMV_API int spmv_export_bytes(spmv_handle h, int32_t array_id, int64_t *bytes);
+
+/*
+ * Copy an internal array (see spmv_array_id) into the caller's device
+ * buffer d_dst of `bytes` bytes (must equal spmv_export_bytes).  Stream-
+ * ordered device-to-device copy.  For tests of the conversions.
+ */
+SPMV_API int spmv_export(spmv_handle h, int32_t array_id, void *d_dst, int64_t bytes,
+                void *stream);
+
+/* Frees every device array of the handle.  NULL is accepted. */
+SPMV_API int spmv_destroy(spmv_handle h);
+
+/* Message of the last failing call on this thread ("" if none). */
+SPMV_API const char *spmv_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPMV_GB300_SPMV_H */

@@ -1,0 +1,180 @@
+"""Thin Python binding of the C ABI in include/spmv.h (argument marshalling).
+
+Every function here has the name of the C entry point it calls and only
+converts arguments: torch tensors become device pointers, the current torch
+CUDA stream becomes the stream argument, status codes become SpmvError.
+All computation happens in libspmv_gb300.so; if the library is missing the
+calls raise instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libspmv_gb300.so")
+
+SPMV_OK = 0
+STATUS_NAMES = {0: "SPMV_OK", -1: "SPMV_ERR_INVALID", -2: "SPMV_ERR_OOM", -3: "SPMV_ERR_CUDA",
+                -4: "SPMV_ERR_UNSUPPORTED", -5: "SPMV_ERR_BOUNDS", -6: "SPMV_ERR_TIMEOUT"}
+SPMV_F64, SPMV_F32, SPMV_BF16 = 0, 1, 2
+FMT_CSR, FMT_ELL, FMT_COO, FMT_HYB, FMT_BSR = 0, 1, 2, 3, 4
+FORMAT_NAMES = {FMT_CSR: "csr", FMT_ELL: "ell", FMT_COO: "coo", FMT_HYB: "hyb", FMT_BSR: "bsr"}
+TPR_SPLIT = -1
+(ARR_CSR_ROWPTR, ARR_CSR_COLIDX, ARR_CSR_VALS, ARR_ELL_COLIDX, ARR_ELL_VALS, ARR_COO_ROWS,
+ ARR_COO_COLS, ARR_COO_VALS, ARR_BSR_ROWPTR, ARR_BSR_COLIDX, ARR_BSR_VALS, ARR_ELL_PITCH) = range(12)
+
+# every entry point include/spmv.h declares (checked by the CPU test suite)
+EXPORTED = ("spmv_config_default", "spmv_create", "spmv_set_config", "spmv_get_config",
+            "spmv_get_info", "spmv_run", "spmv_export_bytes", "spmv_export", "spmv_destroy",
+            "spmv_last_error")
+
+
+class SpmvError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class spmv_config(ctypes.Structure):
+    _fields_ = [("format", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
+                ("threads_per_row", ctypes.c_int32), ("unroll", ctypes.c_int32),
+                ("regcap", ctypes.c_int32), ("carveout", ctypes.c_int32),
+                ("bsr_block", ctypes.c_int32), ("hyb_ell_width", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class spmv_info(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("max_row", ctypes.c_int64), ("ell_width", ctypes.c_int64),
+                ("hyb_coo_nnz", ctypes.c_int64), ("bsr_blocks", ctypes.c_int64),
+                ("format_bytes", ctypes.c_int64), ("value_type", ctypes.c_int32),
+                ("format", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_VP = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I32 = ctypes.c_int32
+_D = ctypes.c_double
+
+
+def load_library(path: str | None = None):
+    """Load libspmv_gb300.so (built by build.py); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise FileNotFoundError(
+            f"{path} is missing: build it with paper_2302_05662_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    sig = {
+        "spmv_config_default": (None, [ctypes.POINTER(spmv_config), _I32]),
+        "spmv_create": (ctypes.c_int, [ctypes.POINTER(_VP), _I64, _I64, _I64, _VP, _VP, _VP, _I32,
+                                       ctypes.POINTER(spmv_config), _VP]),
+        "spmv_set_config": (ctypes.c_int, [_VP, ctypes.POINTER(spmv_config), _VP]),
+        "spmv_get_config": (ctypes.c_int, [_VP, ctypes.POINTER(spmv_config)]),
+        "spmv_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(spmv_info)]),
+        "spmv_run": (ctypes.c_int, [_VP, _D, _VP, _D, _VP, _VP]),
+        "spmv_export_bytes": (ctypes.c_int, [_VP, _I32, ctypes.POINTER(_I64)]),
+        "spmv_export": (ctypes.c_int, [_VP, _I32, _VP, _I64, _VP]),
+        "spmv_destroy": (ctypes.c_int, [_VP]),
+        "spmv_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != SPMV_OK:
+        raise SpmvError(status, spmv_last_error())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def value_type_of(dtype) -> int:
+    import torch
+    return {torch.float64: SPMV_F64, torch.float32: SPMV_F32, torch.bfloat16: SPMV_BF16}[dtype]
+
+
+def make_config(format=FMT_CSR, **kw) -> spmv_config:
+    """spmv_config with library defaults, then overridden by keyword fields."""
+    cfg = spmv_config()
+    load_library().spmv_config_default(ctypes.byref(cfg), int(format))
+    for k, v in kw.items():
+        setattr(cfg, k, int(v))
+    return cfg
+
+
+def spmv_last_error() -> str:
+    return load_library().spmv_last_error().decode(errors="replace")
+
+
+def spmv_create(m: int, n: int, rows, cols, vals, cfg: spmv_config | None = None, stream=None) -> int:
+    """Handle from device COO triplets (int32 rows/cols, f64/f32/bf16 vals)."""
+    lib = load_library()
+    h = _VP()
+    nnz = int(rows.numel()) if rows is not None else 0
+    vt = value_type_of(vals.dtype)
+    _check(lib.spmv_create(ctypes.byref(h), int(m), int(n), nnz, _ptr(rows), _ptr(cols), _ptr(vals), vt,
+                           ctypes.byref(cfg) if cfg is not None else None, _stream(stream)))
+    return h.value
+
+
+def spmv_set_config(h: int, cfg: spmv_config, stream=None):
+    _check(load_library().spmv_set_config(h, ctypes.byref(cfg), _stream(stream)))
+
+
+def spmv_get_config(h: int) -> spmv_config:
+    cfg = spmv_config()
+    _check(load_library().spmv_get_config(h, ctypes.byref(cfg)))
+    return cfg
+
+
+def spmv_get_info(h: int) -> spmv_info:
+    info = spmv_info()
+    _check(load_library().spmv_get_info(h, ctypes.byref(info)))
+    return info
+
+
+def spmv_run(h: int, alpha: float, x, beta: float, y, stream=None):
+    """y <- alpha*A*x + beta*y on the device (x, y: torch CUDA tensors)."""
+    _check(load_library().spmv_run(h, float(alpha), _ptr(x), float(beta), _ptr(y), _stream(stream)))
+
+
+def spmv_export_bytes(h: int, array_id: int) -> int:
+    b = _I64()
+    _check(load_library().spmv_export_bytes(h, int(array_id), ctypes.byref(b)))
+    return b.value
+
+
+def spmv_export(h: int, array_id: int, out, stream=None):
+    """Copy an internal array into the device tensor `out` (exact size)."""
+    nbytes = out.numel() * out.element_size()
+    _check(load_library().spmv_export(h, int(array_id), _ptr(out), nbytes, _stream(stream)))
+
+
+def spmv_destroy(h: int):
+    if h:
+        _check(load_library().spmv_destroy(h))

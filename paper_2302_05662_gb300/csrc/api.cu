@@ -1,0 +1,432 @@
+// C ABI of the SpMV engine (include/spmv.h): handle life cycle, format
+// selection, and dispatch of y = alpha*A*x + beta*y to the kernel families.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <utility>
+
+#include "internal.cuh"
+
+namespace spmv {
+
+namespace {
+thread_local char g_err[512] = "";
+}
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+}
+
+int cuda_status(cudaError_t e, const char *what) {
+    set_error("%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();  // clear the sticky-free allocation error
+        return SPMV_ERR_OOM;
+    }
+    return SPMV_ERR_CUDA;
+}
+
+namespace {
+std::mutex g_attr_mu;
+std::map<std::pair<const void *, int>, int> g_occ;
+std::map<const void *, int> g_carve;
+}  // namespace
+
+int resident_blocks(const void *kernel, int threads) {
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    auto key = std::make_pair(kernel, threads * 64 + dev);
+    auto it = g_occ.find(key);
+    if (it != g_occ.end()) return it->second;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, 0) != cudaSuccess || nb < 1) {
+        cudaGetLastError();
+        nb = 1;
+    }
+    g_occ[key] = nb;
+    return nb;
+}
+
+int apply_carveout(const void *kernel, int carveout) {
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    auto it = g_carve.find(kernel);
+    const int current = it == g_carve.end() ? -1 : it->second;
+    if (current == carveout) return SPMV_OK;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         carveout < 0 ? (int)cudaSharedmemCarveoutDefault : carveout);
+    if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute(carveout)");
+    g_carve[kernel] = carveout;
+    // resident block counts may change with the carveout
+    for (auto i = g_occ.begin(); i != g_occ.end();) {
+        if (i->first.first == kernel) i = g_occ.erase(i);
+        else ++i;
+    }
+    return SPMV_OK;
+}
+
+namespace {
+
+bool pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
+
+// default threads per row: the power of two nearest a quarter of the mean
+// row length (1..32), so each lane sums several entries sequentially before
+// the cross-lane reduction, whose adds are costly in fp64
+int default_tpr(const spmv_matrix *h) {
+    const double q = h->m ? (double)h->nnz / (double)h->m / 4.0 : 1.0;
+    const double e = q > 1.0 ? std::round(std::log2(q)) : 0.0;
+    return 1 << (int)std::min(5.0, e);
+}
+
+// Fills defaults and validates; returns SPMV_ERR_INVALID on a bad field.
+int resolve_config(const spmv_matrix *h, const spmv_config *in, spmv_config *out) {
+    spmv_config c;
+    spmv_config_default(&c, SPMV_FMT_CSR);
+    if (in) {
+        c = *in;
+        if (c.threads_per_block == 0) c.threads_per_block = 256;
+        if (c.unroll == 0) c.unroll = 2;
+        if (c.regcap == 0) c.regcap = 64;
+        if (c.bsr_block == 0) c.bsr_block = 4;
+    }
+    if (c.format < SPMV_FMT_CSR || c.format > SPMV_FMT_BSR) {
+        set_error("config: unknown format %d", c.format);
+        return SPMV_ERR_INVALID;
+    }
+    if (!pow2_in(c.threads_per_block, 32, 1024)) {
+        set_error("config: threads_per_block %d is not a power of two in [32, 1024]", c.threads_per_block);
+        return SPMV_ERR_INVALID;
+    }
+    if (c.unroll != 1 && c.unroll != 2 && c.unroll != 4) {
+        set_error("config: unroll %d not in {1, 2, 4}", c.unroll);
+        return SPMV_ERR_INVALID;
+    }
+    if (c.regcap != 32 && c.regcap != 64) {
+        set_error("config: regcap %d not in {32, 64}", c.regcap);
+        return SPMV_ERR_INVALID;
+    }
+    if (c.carveout < -1 || c.carveout > 100) {
+        set_error("config: carveout %d not in [-1, 100]", c.carveout);
+        return SPMV_ERR_INVALID;
+    }
+    if (c.bsr_block != 2 && c.bsr_block != 4) {
+        set_error("config: bsr_block %d not in {2, 4}", c.bsr_block);
+        return SPMV_ERR_INVALID;
+    }
+    if (c.hyb_ell_width < 0) {
+        set_error("config: negative hyb_ell_width");
+        return SPMV_ERR_INVALID;
+    }
+    switch (c.format) {
+    case SPMV_FMT_CSR:
+        if (c.threads_per_row == 0) c.threads_per_row = default_tpr(h);
+        if (c.threads_per_row != SPMV_TPR_SPLIT && !pow2_in(c.threads_per_row, 1, 32)) {
+            set_error("config: CSR threads_per_row %d not in {1..32 powers of two, -1}", c.threads_per_row);
+            return SPMV_ERR_INVALID;
+        }
+        break;
+    case SPMV_FMT_BSR:
+        if (c.threads_per_row == 0) c.threads_per_row = 1;
+        if (!pow2_in(c.threads_per_row, 1, 8)) {
+            set_error("config: BSR blocks per row group %d not in {1, 2, 4, 8}", c.threads_per_row);
+            return SPMV_ERR_INVALID;
+        }
+        break;
+    default:
+        if (c.threads_per_row != 0 && c.threads_per_row != 1) {
+            set_error("config: threads_per_row must be 0 or 1 for ELL, COO and HYB");
+            return SPMV_ERR_INVALID;
+        }
+        c.threads_per_row = 1;
+        break;
+    }
+    *out = c;
+    return SPMV_OK;
+}
+
+int runner(const spmv_matrix *h, int kind, double alpha, const void *x, double beta, void *y, cudaStream_t s) {
+    switch (h->vt) {
+    case SPMV_F64: return run_kernels_f64(kind, h, alpha, x, beta, y, s);
+    case SPMV_F32: return run_kernels_f32(kind, h, alpha, x, beta, y, s);
+    default: return run_kernels_bf16(kind, h, alpha, x, beta, y, s);
+    }
+}
+
+void destroy_all(spmv_matrix *h) {
+    free_packed(h);
+    if (h->rowptr) cudaFree(h->rowptr);
+    if (h->colidx) cudaFree(h->colidx);
+    if (h->vals) cudaFree(h->vals);
+    h->rowptr = h->colidx = nullptr;
+    h->vals = nullptr;
+}
+
+}  // namespace
+}  // namespace spmv
+
+using namespace spmv;
+
+extern "C" {
+
+void spmv_config_default(spmv_config *cfg, int32_t format) {
+    if (!cfg) return;
+    cfg->format = format;
+    cfg->threads_per_block = 256;
+    cfg->threads_per_row = 0;
+    cfg->unroll = 2;
+    cfg->regcap = 64;
+    cfg->carveout = -1;
+    cfg->bsr_block = 4;
+    cfg->hyb_ell_width = 0;
+}
+
+const char *spmv_last_error(void) { return g_err; }
+
+int spmv_create(spmv_handle *out, int64_t m, int64_t n, int64_t nnz, const int32_t *d_rows, const int32_t *d_cols,
+                const void *d_vals, int32_t value_type, const spmv_config *cfg, void *stream) {
+    g_err[0] = 0;
+    if (!out) {
+        set_error("spmv_create: NULL output handle");
+        return SPMV_ERR_INVALID;
+    }
+    *out = nullptr;
+    if (m < 0 || n < 0 || nnz < 0) {
+        set_error("spmv_create: negative size");
+        return SPMV_ERR_INVALID;
+    }
+    if (value_type != SPMV_F64 && value_type != SPMV_F32 && value_type != SPMV_BF16) {
+        set_error("spmv_create: unknown value type %d", value_type);
+        return SPMV_ERR_INVALID;
+    }
+    if (nnz > 0 && (!d_rows || !d_cols || !d_vals)) {
+        set_error("spmv_create: NULL triplet array with nnz > 0");
+        return SPMV_ERR_INVALID;
+    }
+    if (m >= (int64_t(1) << 31) || n >= (int64_t(1) << 31) || nnz >= (int64_t(1) << 31)) {
+        set_error("spmv_create: m, n and nnz must be below 2^31");
+        return SPMV_ERR_UNSUPPORTED;
+    }
+    if (nnz > 0 && (m == 0 || n == 0)) {
+        set_error("spmv_create: nonzeros in an empty matrix");
+        return SPMV_ERR_INVALID;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    spmv_matrix *h = new (std::nothrow) spmv_matrix();
+    if (!h) {
+        set_error("spmv_create: host allocation failed");
+        return SPMV_ERR_OOM;
+    }
+    h->m = m;
+    h->n = n;
+    h->nnz = nnz;
+    h->vt = value_type;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        int st = cuda_status(e, "device query");
+        delete h;
+        return st;
+    }
+    int st = build_csr(h, d_rows, d_cols, d_vals, s);
+    spmv_config rc;
+    if (st == SPMV_OK) st = resolve_config(h, cfg, &rc);
+    if (st == SPMV_OK) st = pack_format(h, rc, s);
+    if (st != SPMV_OK) {
+        destroy_all(h);
+        delete h;
+        return st;
+    }
+    *out = h;
+    return SPMV_OK;
+}
+
+int spmv_set_config(spmv_handle h, const spmv_config *cfg, void *stream) {
+    g_err[0] = 0;
+    if (!h) {
+        set_error("spmv_set_config: NULL handle");
+        return SPMV_ERR_INVALID;
+    }
+    spmv_config rc;
+    SPMV_TRY(resolve_config(h, cfg, &rc));
+    int st = pack_format(h, rc, (cudaStream_t)stream);
+    if (st != SPMV_OK) {
+        // leave a usable handle: fall back to plain CSR
+        spmv_config csr;
+        spmv_config_default(&csr, SPMV_FMT_CSR);
+        spmv_config rcsr;
+        if (resolve_config(h, &csr, &rcsr) == SPMV_OK) {
+            char saved[512];
+            std::strncpy(saved, g_err, sizeof saved);
+            saved[sizeof saved - 1] = 0;
+            pack_format(h, rcsr, (cudaStream_t)stream);
+            std::strncpy(g_err, saved, sizeof g_err);
+        }
+    }
+    return st;
+}
+
+int spmv_get_config(spmv_handle h, spmv_config *out) {
+    if (!h || !out) {
+        set_error("spmv_get_config: NULL argument");
+        return SPMV_ERR_INVALID;
+    }
+    *out = h->cfg;
+    return SPMV_OK;
+}
+
+int spmv_get_info(spmv_handle h, spmv_info *out) {
+    if (!h || !out) {
+        set_error("spmv_get_info: NULL argument");
+        return SPMV_ERR_INVALID;
+    }
+    std::memset(out, 0, sizeof *out);
+    out->m = h->m;
+    out->n = h->n;
+    out->nnz = h->nnz;
+    out->max_row = h->max_row;
+    out->value_type = h->vt;
+    out->format = h->cfg.format;
+    const int64_t vs = (int64_t)value_size(h->vt);
+    switch (h->cfg.format) {
+    case SPMV_FMT_CSR:
+        out->format_bytes = h->nnz * (vs + 4) + 4 * (h->m + 1);
+        break;
+    case SPMV_FMT_ELL:
+        out->ell_width = h->ell_width;
+        out->format_bytes = h->ell_width * h->ell_pitch * (vs + 4);
+        break;
+    case SPMV_FMT_COO:
+        out->format_bytes = h->nnz * (vs + 8);
+        break;
+    case SPMV_FMT_HYB:
+        out->ell_width = h->ell_width;
+        out->hyb_coo_nnz = h->hyb_nnz;
+        out->format_bytes = h->ell_width * h->ell_pitch * (vs + 4) + h->hyb_nnz * (vs + 8);
+        break;
+    case SPMV_FMT_BSR:
+        out->bsr_blocks = h->bsr_blocks;
+        out->format_bytes = h->bsr_blocks * (vs * h->bsr_r * h->bsr_r + 4) + 4 * (h->bsr_mb + 1);
+        break;
+    }
+    return SPMV_OK;
+}
+
+int spmv_run(spmv_handle h, double alpha, const void *d_x, double beta, void *d_y, void *stream) {
+    if (!h) {
+        set_error("spmv_run: NULL handle");
+        return SPMV_ERR_INVALID;
+    }
+    if ((h->m > 0 && !d_y) || (h->n > 0 && h->nnz > 0 && !d_x)) {
+        set_error("spmv_run: NULL vector");
+        return SPMV_ERR_INVALID;
+    }
+    if (h->m == 0) return SPMV_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (h->nnz == 0) return runner(h, RUN_SCALE, alpha, d_x, beta, d_y, s);
+    switch (h->cfg.format) {
+    case SPMV_FMT_CSR:
+        return runner(h, h->cfg.threads_per_row == SPMV_TPR_SPLIT ? RUN_CSR_SPLIT : RUN_CSR_VECTOR, alpha, d_x, beta,
+                      d_y, s);
+    case SPMV_FMT_ELL: return runner(h, RUN_ELL, alpha, d_x, beta, d_y, s);
+    case SPMV_FMT_COO: return runner(h, RUN_COO, alpha, d_x, beta, d_y, s);
+    case SPMV_FMT_HYB: return runner(h, RUN_HYB, alpha, d_x, beta, d_y, s);
+    case SPMV_FMT_BSR: return runner(h, RUN_BSR, alpha, d_x, beta, d_y, s);
+    }
+    set_error("spmv_run: bad format");
+    return SPMV_ERR_INVALID;
+}
+
+namespace {
+int array_of(spmv_handle h, int32_t id, const void **ptr, int64_t *bytes) {
+    const int64_t vs = (int64_t)value_size(h->vt);
+    const bool hyb = h->cfg.format == SPMV_FMT_HYB;
+    *ptr = nullptr;
+    *bytes = 0;
+    switch (id) {
+    case SPMV_ARR_CSR_ROWPTR: *ptr = h->rowptr; *bytes = 4 * (h->m + 1); break;
+    case SPMV_ARR_CSR_COLIDX: *ptr = h->colidx; *bytes = 4 * h->nnz; break;
+    case SPMV_ARR_CSR_VALS: *ptr = h->vals; *bytes = vs * h->nnz; break;
+    case SPMV_ARR_ELL_COLIDX:
+        if (h->ell_col) { *ptr = h->ell_col; *bytes = 4 * h->ell_width * h->ell_pitch; }
+        break;
+    case SPMV_ARR_ELL_VALS:
+        if (h->ell_val) { *ptr = h->ell_val; *bytes = vs * h->ell_width * h->ell_pitch; }
+        break;
+    case SPMV_ARR_COO_ROWS:
+        if (hyb) { *ptr = h->hyb_rows; *bytes = 4 * h->hyb_nnz; }
+        else if (h->coo_rows) { *ptr = h->coo_rows; *bytes = 4 * h->nnz; }
+        break;
+    case SPMV_ARR_COO_COLS:
+        if (hyb) { *ptr = h->hyb_cols; *bytes = 4 * h->hyb_nnz; }
+        else if (h->coo_rows) { *ptr = h->colidx; *bytes = 4 * h->nnz; }
+        break;
+    case SPMV_ARR_COO_VALS:
+        if (hyb) { *ptr = h->hyb_vals; *bytes = vs * h->hyb_nnz; }
+        else if (h->coo_rows) { *ptr = h->vals; *bytes = vs * h->nnz; }
+        break;
+    case SPMV_ARR_BSR_ROWPTR:
+        if (h->bsr_rowptr) { *ptr = h->bsr_rowptr; *bytes = 4 * (h->bsr_mb + 1); }
+        break;
+    case SPMV_ARR_BSR_COLIDX:
+        if (h->bsr_col) { *ptr = h->bsr_col; *bytes = 4 * h->bsr_blocks; }
+        break;
+    case SPMV_ARR_BSR_VALS:
+        if (h->bsr_val) { *ptr = h->bsr_val; *bytes = vs * h->bsr_blocks * h->bsr_r * h->bsr_r; }
+        break;
+    case SPMV_ARR_ELL_PITCH: *bytes = h->ell_pitch; break;
+    default:
+        set_error("spmv_export: unknown array id %d", id);
+        return SPMV_ERR_INVALID;
+    }
+    return SPMV_OK;
+}
+}  // namespace
+
+int spmv_export_bytes(spmv_handle h, int32_t array_id, int64_t *bytes) {
+    if (!h || !bytes) {
+        set_error("spmv_export_bytes: NULL argument");
+        return SPMV_ERR_INVALID;
+    }
+    const void *p;
+    return array_of(h, array_id, &p, bytes);
+}
+
+int spmv_export(spmv_handle h, int32_t array_id, void *d_dst, int64_t bytes, void *stream) {
+    if (!h) {
+        set_error("spmv_export: NULL handle");
+        return SPMV_ERR_INVALID;
+    }
+    if (array_id == SPMV_ARR_ELL_PITCH) {
+        set_error("spmv_export: the pitch is a size query only");
+        return SPMV_ERR_INVALID;
+    }
+    const void *p;
+    int64_t have;
+    SPMV_TRY(array_of(h, array_id, &p, &have));
+    if (bytes != have) {
+        set_error("spmv_export: %lld bytes requested, array holds %lld", (long long)bytes, (long long)have);
+        return SPMV_ERR_INVALID;
+    }
+    if (have == 0) return SPMV_OK;
+    if (!d_dst) {
+        set_error("spmv_export: NULL destination");
+        return SPMV_ERR_INVALID;
+    }
+    SPMV_CUDA_TRY(cudaMemcpyAsync(d_dst, p, (size_t)have, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return SPMV_OK;
+}
+
+int spmv_destroy(spmv_handle h) {
+    if (!h) return SPMV_OK;
+    destroy_all(h);  // cudaFree waits for work still using the arrays
+    delete h;
+    return SPMV_OK;
+}
+
+}  // extern "C"

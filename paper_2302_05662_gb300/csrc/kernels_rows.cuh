@@ -1,0 +1,287 @@
+// Row-parallel SpMV kernels: CSR vector (threads-per-row lanes per row),
+// column-major ELL (thread per row) and BSR (lanes per block row).
+//
+// Each computes y = alpha * A x + beta * y (Section 2.2) for the storage
+// layouts of Section 2.3.  Kernel parameters are template arguments, so the
+// paper's compile-time knobs (Section 4: register cap, block size) and the
+// threads-per-row / unroll knobs become pre-built variants selected at run
+// time instead of recompilation.
+#pragma once
+
+#include "combine.cuh"
+
+namespace spmv {
+
+constexpr unsigned FULLMASK = 0xffffffffu;
+
+// ---------------------------------------------------------------------------
+// CSR: TPR lanes share a row (Section 2.3: warp lanes coordinate to add the
+// per-thread partial sums).  A warp takes 32 consecutive rows, reads their
+// bounds with one coalesced load, then works through them RPW = 32/TPR rows
+// at a time, each lane keeping UNROLL loads in flight.  Rows longer than
+// long_threshold are left to k_csr_long.  All loops are warp-uniform, so the
+// shuffle reduction always has every lane.
+// ---------------------------------------------------------------------------
+template <typename V, typename T, int TPR, int UNROLL, int REGCAP>
+__global__ void __launch_bounds__(1024) __maxnreg__(REGCAP)
+k_csr_vector(int64_t m, const int *__restrict__ rowptr, const int *__restrict__ colidx,
+             const V *__restrict__ vals, const T *__restrict__ x, T *__restrict__ y, T alpha, T beta,
+             int long_threshold) {
+    const Epi<T> ep(alpha, beta);
+    constexpr int RPW = 32 / TPR;  // rows per warp per step
+    const int lane = threadIdx.x & 31;
+    const int sub = lane % TPR, grp = lane / TPR;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = warp * 32; base < m; base += nwarps * 32) {
+        const int64_t rr = base + lane;
+        const int my_s = rr < m ? __ldg(rowptr + rr) : 0;
+        const int my_e = rr < m ? __ldg(rowptr + rr + 1) : 0;
+#pragma unroll 1
+        for (int g = 0; g < TPR; ++g) {
+            const int src = g * RPW + grp;
+            const int s = __shfl_sync(FULLMASK, my_s, src);
+            const int e = __shfl_sync(FULLMASK, my_e, src);
+            const int64_t row = base + src;
+            const bool skip = row >= m || e - s > long_threshold;
+            T acc = T(0);
+            if (!skip) {
+                for (int k = s + sub; k < e; k += TPR * UNROLL) {
+                    int c[UNROLL];
+                    T v[UNROLL];
+#pragma unroll
+                    for (int u = 0; u < UNROLL; ++u) {
+                        const int kk = k + u * TPR;
+                        c[u] = kk < e ? ld_s(colidx + kk) : -1;
+                        v[u] = kk < e ? ld_val(vals + kk) : T(0);
+                    }
+#pragma unroll
+                    for (int u = 0; u < UNROLL; ++u)
+                        if (c[u] >= 0) acc += v[u] * ld_x(x, c[u]);
+                }
+            }
+#pragma unroll
+            for (int off = TPR / 2; off > 0; off >>= 1) acc += __shfl_down_sync(FULLMASK, acc, off, TPR);
+            if (sub == 0 && !skip) ep.store(y, row, acc);
+        }
+    }
+}
+
+// Long CSR rows: one thread block per segment of a long row; segments of one
+// row are joined through the partials (fixed order).
+template <typename V, typename T>
+__global__ void __launch_bounds__(256)
+k_csr_long(int64_t nseg, const int *__restrict__ seg_row, const int *__restrict__ seg_begin,
+           const int *__restrict__ seg_end, const int *__restrict__ seg_c0, const int *__restrict__ seg_c1,
+           const int *__restrict__ colidx, const V *__restrict__ vals, const T *__restrict__ x, T *__restrict__ y,
+           T alpha, T beta, const PartialsT<T> P) {
+    const Epi<T> ep(alpha, beta);
+    __shared__ T red[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t k = blockIdx.x; k < nseg; k += gridDim.x) {
+        const int b = __ldg(seg_begin + k), e = __ldg(seg_end + k);
+        T acc = T(0);
+        for (int i = b + threadIdx.x; i < e; i += 256 * 4) {
+            int c[4];
+            T v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int ii = i + u * 256;
+                c[u] = ii < e ? ld_s(colidx + ii) : -1;
+                v[u] = ii < e ? ld_val(vals + ii) : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (c[u] >= 0) acc += v[u] * ld_x(x, c[u]);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(FULLMASK, acc, off);
+        if (lane == 0) red[warp] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            T t = T(0);
+#pragma unroll
+            for (int w = 0; w < 8; ++w) t += red[w];
+            const int row = __ldg(seg_row + k);
+            const int64_t c0 = __ldg(seg_c0 + k), c1 = __ldg(seg_c1 + k);
+            T total = t;
+            if (c0 == c1 || join_partial<T>(k, c0, c1, 0, t, P, &total)) ep.store(y, row, total);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// ELL, column-major [width][pitch] (Section 2.3: m x max_nnz Data and Column
+// Index matrices).  Padding has column -1 and rows are left-packed, so a
+// thread stops at its first padding slot and reads no padding values.
+// ---------------------------------------------------------------------------
+template <typename V, typename T, int UNROLL>
+__global__ void __launch_bounds__(1024)
+k_ell(int64_t m, int64_t width, int64_t pitch, const int *__restrict__ col, const V *__restrict__ val,
+      const T *__restrict__ x, T *__restrict__ y, T alpha, T beta) {
+    const Epi<T> ep(alpha, beta);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < m; r += stride) {
+        T acc = T(0);
+        int64_t k = 0;
+        bool done = false;
+        for (; !done && k + UNROLL <= width; k += UNROLL) {
+            int c[UNROLL];
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) c[u] = ld_s(col + (k + u) * pitch + r);
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) {
+                if (c[u] >= 0) acc += ld_val(val + (k + u) * pitch + r) * ld_x(x, c[u]);
+                else done = true;
+            }
+        }
+        for (; !done && k < width; ++k) {
+            const int c = ld_s(col + k * pitch + r);
+            if (c < 0) break;
+            acc += ld_val(val + k * pitch + r) * ld_x(x, c);
+        }
+        ep.store(y, r, acc);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// BSR with R x R row-major blocks (the blocked ELL of Section 2.3 stored by
+// block rows).  A group of R*S lanes owns a block row: lane (s, i) takes
+// row i of every S-th block, so a warp reads whole blocks contiguously.
+// ---------------------------------------------------------------------------
+template <int R, typename V, typename T> struct BlockRow;
+template <> struct BlockRow<4, double, double> {
+    static __device__ __forceinline__ void load(const double *p, double (&o)[4]) {
+        double2 a = ld_s(reinterpret_cast<const double2 *>(p));
+        double2 b = ld_s(reinterpret_cast<const double2 *>(p) + 1);
+        o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+    }
+};
+template <> struct BlockRow<2, double, double> {
+    static __device__ __forceinline__ void load(const double *p, double (&o)[2]) {
+        double2 a = ld_s(reinterpret_cast<const double2 *>(p));
+        o[0] = a.x; o[1] = a.y;
+    }
+};
+template <> struct BlockRow<4, float, float> {
+    static __device__ __forceinline__ void load(const float *p, float (&o)[4]) {
+        float4 a = ld_s(reinterpret_cast<const float4 *>(p));
+        o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+    }
+};
+template <> struct BlockRow<2, float, float> {
+    static __device__ __forceinline__ void load(const float *p, float (&o)[2]) {
+        float2 a = ld_s(reinterpret_cast<const float2 *>(p));
+        o[0] = a.x; o[1] = a.y;
+    }
+};
+template <> struct BlockRow<4, __nv_bfloat16, float> {
+    static __device__ __forceinline__ void load(const __nv_bfloat16 *p, float (&o)[4]) {
+        uint2 w = ld_s(reinterpret_cast<const uint2 *>(p));
+        o[0] = bf16lo(w.x); o[1] = bf16hi(w.x); o[2] = bf16lo(w.y); o[3] = bf16hi(w.y);
+    }
+};
+template <> struct BlockRow<2, __nv_bfloat16, float> {
+    static __device__ __forceinline__ void load(const __nv_bfloat16 *p, float (&o)[2]) {
+        uint32_t w = (uint32_t)ld_s(reinterpret_cast<const int *>(p));
+        o[0] = bf16lo(w); o[1] = bf16hi(w);
+    }
+};
+
+template <typename V, typename T, int R, int S>
+__global__ void __launch_bounds__(1024)
+k_bsr(int64_t mb, int64_t m, int64_t n, const int *__restrict__ browptr, const int *__restrict__ bcol,
+      const V *__restrict__ bval, const T *__restrict__ x, T *__restrict__ y, T alpha, T beta, int long_threshold) {
+    const Epi<T> ep(alpha, beta);
+    constexpr int G = R * S;     // lanes per block row
+    constexpr int GPW = 32 / G;  // block rows per warp per step
+    const int lane = threadIdx.x & 31;
+    const int sub = lane % G, sblk = sub / R, i = sub % R;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = warp * GPW; base < mb; base += nwarps * GPW) {
+        const int64_t br = base + lane / G;
+        T acc = T(0);
+        bool skip = br >= mb;
+        if (!skip) {
+            const int bs = __ldg(browptr + br), be = __ldg(browptr + br + 1);
+            skip = be - bs > long_threshold;
+            // two blocks per step keep more loads in flight
+            for (int b = bs + sblk; !skip && b < be; b += 2 * S) {
+                const bool two = b + S < be;
+                const int64_t c0 = (int64_t)ld_s(bcol + b) * R;
+                const int64_t c1 = two ? (int64_t)ld_s(bcol + b + S) * R : c0;
+                T v0[R], v1[R];
+                BlockRow<R, V, T>::load(bval + (int64_t)b * R * R + i * R, v0);
+                if (two) BlockRow<R, V, T>::load(bval + (int64_t)(b + S) * R * R + i * R, v1);
+#pragma unroll
+                for (int j = 0; j < R; ++j)
+                    if (c0 + j < n) acc += v0[j] * ld_x(x, (int)(c0 + j));
+                if (two) {
+#pragma unroll
+                    for (int j = 0; j < R; ++j)
+                        if (c1 + j < n) acc += v1[j] * ld_x(x, (int)(c1 + j));
+                }
+            }
+        }
+#pragma unroll
+        for (int off = G / 2; off >= R; off >>= 1) acc += __shfl_down_sync(FULLMASK, acc, off, G);
+        if (sblk == 0 && !skip) {
+            const int64_t row = br * R + i;
+            if (row < m) ep.store(y, row, acc);
+        }
+    }
+}
+
+// Long BSR block rows: one thread block per segment of blocks; lane (g, i)
+// takes row i of every (256/R)-th block; rows of a block row are joined
+// across segments through the partials with stride R.
+template <typename V, typename T, int R>
+__global__ void __launch_bounds__(256)
+k_bsr_long(int64_t nseg, const int *__restrict__ seg_row, const int *__restrict__ seg_begin,
+           const int *__restrict__ seg_end, const int *__restrict__ seg_c0, const int *__restrict__ seg_c1,
+           int64_t m, int64_t n, const int *__restrict__ bcol, const V *__restrict__ bval,
+           const T *__restrict__ x, T *__restrict__ y, T alpha, T beta, const PartialsT<T> P) {
+    const Epi<T> ep(alpha, beta);
+    constexpr int G = 256 / R;
+    __shared__ T red[256];
+    const int i = threadIdx.x % R, g = threadIdx.x / R;
+    for (int64_t k = blockIdx.x; k < nseg; k += gridDim.x) {
+        const int b = __ldg(seg_begin + k), e = __ldg(seg_end + k);
+        T acc = T(0);
+        for (int j = b + g; j < e; j += G) {
+            const int64_t c0 = (int64_t)ld_s(bcol + j) * R;
+            T v[R];
+            BlockRow<R, V, T>::load(bval + (int64_t)j * R * R + i * R, v);
+#pragma unroll
+            for (int q = 0; q < R; ++q)
+                if (c0 + q < n) acc += v[q] * ld_x(x, (int)(c0 + q));
+        }
+        red[threadIdx.x] = acc;
+        __syncthreads();
+        for (int st = G / 2; st > 0; st >>= 1) {
+            if (g < st) red[g * R + i] += red[(g + st) * R + i];
+            __syncthreads();
+        }
+        if (threadIdx.x < R) {
+            const int64_t row = (int64_t)__ldg(seg_row + k) * R + i;
+            if (row < m) {
+                const int64_t c0 = __ldg(seg_c0 + k), c1 = __ldg(seg_c1 + k);
+                T total = red[i];
+                if (c0 == c1 || join_partial<T>(k, c0, c1, i, red[i], P, &total))
+                    ep.store(y, row, total);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__global__ void k_scale_y(int64_t m, T *y, T beta) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < m; r += stride)
+        y[r] = beta == T(0) ? T(0) : beta * y[r];
+}
+
+}  // namespace spmv

@@ -1,0 +1,250 @@
+// Host-side launchers for every kernel family, templated on the value type.
+// Each translation unit kernels_<type>.cu instantiates them for one type, so
+// the ~150 kernel variants compile in parallel.
+#pragma once
+
+#include "kernels_rows.cuh"
+#include "kernels_seg.cuh"
+
+namespace spmv {
+
+// occupancy-limited resident blocks per SM for (kernel, block size); cached
+int resident_blocks(const void *kernel, int threads);
+
+// grid of at most one full wave of resident blocks (grid-stride kernels)
+inline int wave_grid(const void *kernel, int threads, int64_t needed_blocks, int sm_count) {
+    const int64_t cap = (int64_t)resident_blocks(kernel, threads) * sm_count;
+    int64_t g = needed_blocks < cap ? needed_blocks : cap;
+    return (int)(g < 1 ? 1 : g);
+}
+
+#define SPMV_LAUNCH_CHECK()                                      \
+    do {                                                         \
+        cudaError_t _e = cudaGetLastError();                     \
+        if (_e != cudaSuccess) return cuda_status(_e, "kernel launch"); \
+    } while (0)
+
+// ------------------------------- long rows ---------------------------------
+template <typename V, typename T>
+int launch_csr_long(const spmv_matrix *h, T alpha, const T *x, T beta, T *y, cudaStream_t s) {
+    const LongRows &L = h->lng;
+    if (L.nseg == 0) return SPMV_OK;
+    auto kern = k_csr_long<V, T>;
+    const int grid = wave_grid((const void *)kern, 256, L.nseg, h->sm_count);
+    kern<<<grid, 256, 0, s>>>(L.nseg, L.seg_row, L.seg_begin, L.seg_end, L.seg_c0, L.seg_c1, h->colidx,
+                              (const V *)h->vals, x, y, alpha, beta, PartialsT<T>::of(L.part));
+    SPMV_LAUNCH_CHECK();
+    return SPMV_OK;
+}
+
+template <typename V, typename T, int R>
+int launch_bsr_long(const spmv_matrix *h, T alpha, const T *x, T beta, T *y, cudaStream_t s) {
+    const LongRows &L = h->lng;
+    if (L.nseg == 0) return SPMV_OK;
+    auto kern = k_bsr_long<V, T, R>;
+    const int grid = wave_grid((const void *)kern, 256, L.nseg, h->sm_count);
+    kern<<<grid, 256, 0, s>>>(L.nseg, L.seg_row, L.seg_begin, L.seg_end, L.seg_c0, L.seg_c1, h->m, h->n, h->bsr_col,
+                              (const V *)h->bsr_val, x, y, alpha, beta, PartialsT<T>::of(L.part));
+    SPMV_LAUNCH_CHECK();
+    return SPMV_OK;
+}
+
+// ------------------------------- CSR vector --------------------------------
+template <typename V, typename T, int TPR, int U, int RC>
+int launch_csr_vector(const spmv_matrix *h, T alpha, const T *x, T beta, T *y, cudaStream_t s) {
+    auto kern = k_csr_vector<V, T, TPR, U, RC>;
+    const int tpb = h->cfg.threads_per_block;
+    SPMV_TRY(apply_carveout((const void *)kern, h->cfg.carveout));
+    const int64_t rows_per_block = tpb / TPR;
+    const int grid = wave_grid((const void *)kern, tpb, (h->m + rows_per_block - 1) / rows_per_block, h->sm_count);
+    const int thr = h->lng.nseg > 0 ? (int)h->lng.threshold : 0x7fffffff;
+    kern<<<grid, tpb, 0, s>>>(h->m, h->rowptr, h->colidx, (const V *)h->vals, x, y, alpha, beta, thr);
+    SPMV_LAUNCH_CHECK();
+    return launch_csr_long<V, T>(h, alpha, x, beta, y, s);
+}
+
+template <typename V, typename T, int TPR, int U>
+int csr_vector_rc(const spmv_matrix *h, T a, const T *x, T b, T *y, cudaStream_t s) {
+    return h->cfg.regcap == 32 ? launch_csr_vector<V, T, TPR, U, 32>(h, a, x, b, y, s)
+                               : launch_csr_vector<V, T, TPR, U, 64>(h, a, x, b, y, s);
+}
+
+template <typename V, typename T, int TPR>
+int csr_vector_u(const spmv_matrix *h, T a, const T *x, T b, T *y, cudaStream_t s) {
+    switch (h->cfg.unroll) {
+    case 1: return csr_vector_rc<V, T, TPR, 1>(h, a, x, b, y, s);
+    case 2: return csr_vector_rc<V, T, TPR, 2>(h, a, x, b, y, s);
+    default: return csr_vector_rc<V, T, TPR, 4>(h, a, x, b, y, s);
+    }
+}
+
+template <int VT>
+int run_csr_vector_vt(const spmv_matrix *h, double alpha, const void *x, double beta, void *y, cudaStream_t s) {
+    using V = typename VT_<VT>::V;
+    using T = typename VT_<VT>::T;
+    const T a = (T)alpha, b = (T)beta;
+    const T *xx = (const T *)x;
+    T *yy = (T *)y;
+    switch (h->cfg.threads_per_row) {
+    case 1: return csr_vector_u<V, T, 1>(h, a, xx, b, yy, s);
+    case 2: return csr_vector_u<V, T, 2>(h, a, xx, b, yy, s);
+    case 4: return csr_vector_u<V, T, 4>(h, a, xx, b, yy, s);
+    case 8: return csr_vector_u<V, T, 8>(h, a, xx, b, yy, s);
+    case 16: return csr_vector_u<V, T, 16>(h, a, xx, b, yy, s);
+    default: return csr_vector_u<V, T, 32>(h, a, xx, b, yy, s);
+    }
+}
+
+// ----------------------------------- ELL -----------------------------------
+template <typename V, typename T, int U>
+int launch_ell(const spmv_matrix *h, int64_t width, T alpha, const T *x, T beta, T *y, cudaStream_t s) {
+    auto kern = k_ell<V, T, U>;
+    const int tpb = h->cfg.threads_per_block;
+    SPMV_TRY(apply_carveout((const void *)kern, h->cfg.carveout));
+    const int grid = wave_grid((const void *)kern, tpb, (h->m + tpb - 1) / tpb, h->sm_count);
+    kern<<<grid, tpb, 0, s>>>(h->m, width, h->ell_pitch, h->ell_col, (const V *)h->ell_val, x, y, alpha, beta);
+    SPMV_LAUNCH_CHECK();
+    return SPMV_OK;
+}
+
+template <int VT>
+int run_ell_vt(const spmv_matrix *h, double alpha, const void *x, double beta, void *y, cudaStream_t s) {
+    using V = typename VT_<VT>::V;
+    using T = typename VT_<VT>::T;
+    const T a = (T)alpha, b = (T)beta;
+    switch (h->cfg.unroll) {
+    case 1: return launch_ell<V, T, 1>(h, h->ell_width, a, (const T *)x, b, (T *)y, s);
+    case 2: return launch_ell<V, T, 2>(h, h->ell_width, a, (const T *)x, b, (T *)y, s);
+    default: return launch_ell<V, T, 4>(h, h->ell_width, a, (const T *)x, b, (T *)y, s);
+    }
+}
+
+// ----------------------------------- BSR -----------------------------------
+template <typename V, typename T, int R, int S>
+int launch_bsr(const spmv_matrix *h, T alpha, const T *x, T beta, T *y, cudaStream_t s) {
+    auto kern = k_bsr<V, T, R, S>;
+    const int tpb = h->cfg.threads_per_block;
+    SPMV_TRY(apply_carveout((const void *)kern, h->cfg.carveout));
+    const int64_t brows_per_block = tpb / (R * S);
+    const int grid =
+        wave_grid((const void *)kern, tpb, (h->bsr_mb + brows_per_block - 1) / brows_per_block, h->sm_count);
+    const int thr = h->lng.nseg > 0 ? (int)h->lng.threshold : 0x7fffffff;
+    kern<<<grid, tpb, 0, s>>>(h->bsr_mb, h->m, h->n, h->bsr_rowptr, h->bsr_col, (const V *)h->bsr_val, x, y, alpha,
+                              beta, thr);
+    SPMV_LAUNCH_CHECK();
+    return launch_bsr_long<V, T, R>(h, alpha, x, beta, y, s);
+}
+
+template <typename V, typename T, int R>
+int bsr_s(const spmv_matrix *h, T a, const T *x, T b, T *y, cudaStream_t s) {
+    switch (h->cfg.threads_per_row) {
+    case 2: return launch_bsr<V, T, R, 2>(h, a, x, b, y, s);
+    case 4: return launch_bsr<V, T, R, 4>(h, a, x, b, y, s);
+    case 8: return launch_bsr<V, T, R, 8>(h, a, x, b, y, s);
+    default: return launch_bsr<V, T, R, 1>(h, a, x, b, y, s);
+    }
+}
+
+template <int VT>
+int run_bsr_vt(const spmv_matrix *h, double alpha, const void *x, double beta, void *y, cudaStream_t s) {
+    using V = typename VT_<VT>::V;
+    using T = typename VT_<VT>::T;
+    const T a = (T)alpha, b = (T)beta;
+    if (h->bsr_r == 2) return bsr_s<V, T, 2>(h, a, (const T *)x, b, (T *)y, s);
+    return bsr_s<V, T, 4>(h, a, (const T *)x, b, (T *)y, s);
+}
+
+// ---------------------------- COO / HYB / split ----------------------------
+template <typename V, typename T, int ITEMS, bool ACCUM>
+int launch_coo(const spmv_matrix *h, int64_t nnz, const int *rows, const int *cols, const V *vals, T alpha,
+               const T *x, T beta, T *y, cudaStream_t s) {
+    auto kern = k_coo_seg<V, T, ITEMS, ACCUM>;
+    const int tpb = ITEMS >= 16 && h->cfg.threads_per_block > 512 ? 512 : h->cfg.threads_per_block;
+    SPMV_TRY(apply_carveout((const void *)kern, h->cfg.carveout));
+    const int64_t chunks = (nnz + 32 * ITEMS - 1) / (32 * ITEMS);
+    const int64_t wpb = tpb / 32;
+    const int grid = wave_grid((const void *)kern, tpb, (chunks + wpb - 1) / wpb, h->sm_count);
+    kern<<<grid, tpb, 0, s>>>(nnz, h->m, rows, cols, vals, x, y, alpha, beta, h->seg.meta0, h->seg.meta1,
+                              PartialsT<T>::of(h->seg.part));
+    SPMV_LAUNCH_CHECK();
+    return SPMV_OK;
+}
+
+template <typename V, typename T, bool ACCUM>
+int coo_items(const spmv_matrix *h, int64_t nnz, const int *rows, const int *cols, const V *vals, T a,
+              const T *x, T b, T *y, cudaStream_t s) {
+    switch (h->seg.items) {
+    case 4: return launch_coo<V, T, 4, ACCUM>(h, nnz, rows, cols, vals, a, x, b, y, s);
+    case 8: return launch_coo<V, T, 8, ACCUM>(h, nnz, rows, cols, vals, a, x, b, y, s);
+    default: return launch_coo<V, T, 16, ACCUM>(h, nnz, rows, cols, vals, a, x, b, y, s);
+    }
+}
+
+template <int VT>
+int run_coo_vt(const spmv_matrix *h, double alpha, const void *x, double beta, void *y, cudaStream_t s) {
+    using V = typename VT_<VT>::V;
+    using T = typename VT_<VT>::T;
+    return coo_items<V, T, false>(h, h->nnz, h->coo_rows, h->colidx, (const V *)h->vals, (T)alpha, (const T *)x,
+                                  (T)beta, (T *)y, s);
+}
+
+template <int VT>
+int run_hyb_vt(const spmv_matrix *h, double alpha, const void *x, double beta, void *y, cudaStream_t s) {
+    using V = typename VT_<VT>::V;
+    using T = typename VT_<VT>::T;
+    SPMV_TRY(run_ell_vt<VT>(h, alpha, x, beta, y, s));
+    if (h->hyb_nnz == 0) return SPMV_OK;
+    return coo_items<V, T, true>(h, h->hyb_nnz, h->hyb_rows, h->hyb_cols, (const V *)h->hyb_vals, (T)alpha,
+                                 (const T *)x, (T)beta, (T *)y, s);
+}
+
+template <typename V, typename T, int ITEMS>
+int launch_split(const spmv_matrix *h, T alpha, const T *x, T beta, T *y, cudaStream_t s) {
+    auto kern = k_csr_split<V, T, ITEMS>;
+    const int tpb = ITEMS >= 16 && h->cfg.threads_per_block > 512 ? 512 : h->cfg.threads_per_block;
+    SPMV_TRY(apply_carveout((const void *)kern, h->cfg.carveout));
+    const int64_t chunks = (h->nnz + 32 * ITEMS - 1) / (32 * ITEMS);
+    const int64_t wpb = tpb / 32;
+    const int grid = wave_grid((const void *)kern, tpb, (chunks + wpb - 1) / wpb, h->sm_count);
+    kern<<<grid, tpb, 0, s>>>(h->nnz, h->m, h->rowptr, h->colidx, (const V *)h->vals, x, y, alpha, beta,
+                              h->seg.meta0, PartialsT<T>::of(h->seg.part));
+    SPMV_LAUNCH_CHECK();
+    return SPMV_OK;
+}
+
+template <int VT>
+int run_csr_split_vt(const spmv_matrix *h, double alpha, const void *x, double beta, void *y, cudaStream_t s) {
+    using V = typename VT_<VT>::V;
+    using T = typename VT_<VT>::T;
+    const T a = (T)alpha, b = (T)beta;
+    switch (h->seg.items) {
+    case 4: return launch_split<V, T, 4>(h, a, (const T *)x, b, (T *)y, s);
+    case 8: return launch_split<V, T, 8>(h, a, (const T *)x, b, (T *)y, s);
+    default: return launch_split<V, T, 16>(h, a, (const T *)x, b, (T *)y, s);
+    }
+}
+
+template <int VT>
+int run_scale_y_vt(int64_t m, double beta, void *y, cudaStream_t s) {
+    using T = typename VT_<VT>::T;
+    if (m == 0) return SPMV_OK;
+    k_scale_y<T><<<(unsigned)((m + 255) / 256 < 4096 ? (m + 255) / 256 : 4096), 256, 0, s>>>(m, (T *)y, (T)beta);
+    SPMV_LAUNCH_CHECK();
+    return SPMV_OK;
+}
+
+#define SPMV_DEFINE_RUNNER(NAME, VT)                                                                 \
+    int NAME(int kind, const spmv_matrix *h, double a, const void *x, double b, void *y, cudaStream_t s) { \
+        switch (kind) {                                                                                  \
+        case RUN_CSR_VECTOR: return run_csr_vector_vt<VT>(h, a, x, b, y, s);                             \
+        case RUN_CSR_SPLIT: return run_csr_split_vt<VT>(h, a, x, b, y, s);                               \
+        case RUN_ELL: return run_ell_vt<VT>(h, a, x, b, y, s);                                           \
+        case RUN_COO: return run_coo_vt<VT>(h, a, x, b, y, s);                                           \
+        case RUN_HYB: return run_hyb_vt<VT>(h, a, x, b, y, s);                                           \
+        case RUN_BSR: return run_bsr_vt<VT>(h, a, x, b, y, s);                                           \
+        case RUN_SCALE: return run_scale_y_vt<VT>(h->m, b, y, s);                                        \
+        }                                                                                                \
+        return SPMV_ERR_INVALID;                                                                         \
+    }
+
+}  // namespace spmv

@@ -325,14 +325,15 @@ def family_matrix(family: str, n_target: int, seed: int,
     raise ValueError(f"unknown family {family!r}")
 
 
-def workload_matrices(scale: str = "full", seed: int = 1):
+def workload_matrices(scale: str = "full", seed: int = 1, only=None):
     """The five structure families of the format-sweep workload.
 
     scale="full": 27-point stencil 128^3 (n = 2,097,152), Poisson(16) rows
     n = 2^20, R-MAT scale 20 edge factor 16, banded n = 2^20 half-width 32,
     block-diagonal 4x4 n = 2^20.  scale="small": the same structures at
     about 2^14 rows, for parity tests the oracle finishes in seconds.
-    Yields (name, Coo) lazily so only one matrix is generated at a time.
+    Yields (name, Coo) lazily so only one matrix is generated at a time;
+    `only` (a name or a collection of names) restricts the set.
     """
     if scale == "full":
         specs = [("stencil27_128^3", lambda r: stencil_3d(128, 27, r)),
@@ -348,7 +349,11 @@ def workload_matrices(scale: str = "full", seed: int = 1):
                  ("blockdiag4_2^14", lambda r: block_diagonal(1 << 14, 4, r))]
     else:
         raise ValueError(scale)
+    if isinstance(only, str):
+        only = {only}
     for k, (name, fn) in enumerate(specs):
+        if only is not None and name not in only:
+            continue
         coo = fn(np.random.default_rng(seed * 1000 + k))
         coo.name = name
         yield name, coo

@@ -1,0 +1,67 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports
+every entry point include/*.h declares; host-side argument checks work
+without touching the device."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_2302_05662_gb300 import binding
+from paper_2302_05662_gb300 import build as build_mod
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build_mod.build()
+    return binding.load_library()
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:SPMV_API\s+)?(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*(spmv_[A-Za-z0-9_]+)\s*\(",
+                             text, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    decl = declared_functions()
+    assert "spmv_create" in decl and "spmv_run" in decl
+    for name in decl:
+        assert hasattr(lib, name), name
+    assert decl == set(binding.EXPORTED)
+
+
+def test_only_the_abi_is_exported(lib):
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--defined-only", binding.LIB_PATH], capture_output=True,
+                         text=True).stdout
+    syms = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    assert declared_functions() <= syms
+    assert not [s for s in syms if s.startswith("_Z")], "C++ symbols leak out of the library"
+
+
+def test_config_default_host_only(lib):
+    cfg = binding.spmv_config()
+    lib.spmv_config_default(ctypes.byref(cfg), binding.FMT_BSR)
+    assert cfg.as_dict() == {"format": 4, "threads_per_block": 256, "threads_per_row": 0, "unroll": 2,
+                             "regcap": 64, "carveout": -1, "bsr_block": 4, "hyb_ell_width": 0}
+
+
+def test_host_argument_errors(lib):
+    h = ctypes.c_void_p()
+    assert lib.spmv_create(ctypes.byref(h), -1, 3, 0, None, None, None, 0, None, None) == -1
+    assert b"negative" in lib.spmv_last_error()
+    assert lib.spmv_create(ctypes.byref(h), 3, 3, 5, None, None, None, 0, None, None) == -1
+    assert lib.spmv_create(ctypes.byref(h), 3, 3, 0, None, None, None, 7, None, None) == -1
+    assert lib.spmv_create(ctypes.byref(h), 1 << 31, 3, 0, None, None, None, 0, None, None) == -4
+    assert lib.spmv_run(None, 1.0, None, 0.0, None, None) == -1
+    assert lib.spmv_destroy(None) == 0
+    assert lib.spmv_get_info(None, None) == -1
