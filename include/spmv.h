@@ -76,8 +76,8 @@ typedef enum {
  *   threads_per_block 32..1024, a power of two (default 256).
  *   threads_per_row   CSR: lanes cooperating on one row, 1/2/4/8/16/32, or
  *                     SPMV_TPR_SPLIT for the nnz-balanced split (default:
- *                     the power of two nearest a quarter of the mean row
- *                     length, capped at 32).  BSR: blocks handled at once per block row,
+ *                     the largest power of two up to 32 that leaves each
+ *                     lane at least 8 entries of a mean-length row).  BSR: blocks handled at once per block row,
  *                     1/2/4/8 (default 1).  Ignored by ELL, COO and HYB.
  *   unroll            1, 2 or 4 (default 2): loads in flight per lane (ELL,
  *                     CSR) or items per lane / 4 (COO, HYB tail, split CSR).

@@ -74,13 +74,14 @@ namespace {
 
 bool pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
 
-// default threads per row: the power of two nearest a quarter of the mean
-// row length (1..32), so each lane sums several entries sequentially before
-// the cross-lane reduction, whose adds are costly in fp64
+// default threads per row: the largest power of two (1..32) that leaves each
+// lane at least eight entries of a mean-length row, so lanes accumulate
+// sequentially and the cross-lane adds (costly in fp64 on this GPU) are few
 int default_tpr(const spmv_matrix *h) {
-    const double q = h->m ? (double)h->nnz / (double)h->m / 4.0 : 1.0;
-    const double e = q > 1.0 ? std::round(std::log2(q)) : 0.0;
-    return 1 << (int)std::min(5.0, e);
+    const double q = h->m ? (double)h->nnz / (double)h->m / 8.0 : 1.0;
+    int t = 1;
+    while (t < 32 && 2.0 * t <= q) t *= 2;
+    return t;
 }
 
 // Fills defaults and validates; returns SPMV_ERR_INVALID on a bad field.

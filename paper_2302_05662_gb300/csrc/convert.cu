@@ -865,7 +865,19 @@ int ensure_seg_scratch(spmv_matrix *h, int items, bool split_csr, cudaStream_t s
 }
 
 int pack_format(spmv_matrix *h, const spmv_config &cfg, cudaStream_t s) {
+    // a change of launch parameters only (block size, register cap, carveout)
+    // keeps the packed arrays
+    const spmv_config &p = h->packed_req;
+    if (h->packed && p.format == cfg.format && p.threads_per_row == cfg.threads_per_row &&
+        p.unroll == cfg.unroll && p.bsr_block == cfg.bsr_block && p.hyb_ell_width == cfg.hyb_ell_width) {
+        const int32_t width = h->cfg.hyb_ell_width;
+        h->cfg = cfg;
+        if (cfg.format == SPMV_FMT_HYB) h->cfg.hyb_ell_width = width;
+        return SPMV_OK;
+    }
     free_packed(h);
+    h->packed = false;
+    h->packed_req = cfg;
     h->cfg = cfg;
     const int items = 4 * cfg.unroll;
     switch (cfg.format) {
@@ -914,6 +926,7 @@ int pack_format(spmv_matrix *h, const spmv_config &cfg, cudaStream_t s) {
         return SPMV_ERR_INVALID;
     }
     SPMV_CUDA_TRY(cudaStreamSynchronize(s));
+    h->packed = true;
     return SPMV_OK;
 }
 

@@ -120,6 +120,14 @@ __device__ __forceinline__ float ld_val(const __nv_bfloat16 *p) {
     return __uint_as_float((uint32_t)ld_s(reinterpret_cast<const unsigned short *>(p)) << 16);
 }
 
+// cached variants (L1-allocating), for access patterns where one lane reads
+// consecutive entries across successive instructions
+__device__ __forceinline__ double ld_val_c(const double *p) { return __ldg(p); }
+__device__ __forceinline__ float ld_val_c(const float *p) { return __ldg(p); }
+__device__ __forceinline__ float ld_val_c(const __nv_bfloat16 *p) {
+    return __uint_as_float((uint32_t)__ldg(reinterpret_cast<const unsigned short *>(p)) << 16);
+}
+
 // N contiguous stored values starting at an N-aligned element (vector loads)
 template <int N>
 __device__ __forceinline__ void ld_vals_vec(const double *p, double (&o)[N]) {
@@ -242,6 +250,8 @@ struct spmv_matrix {
     int64_t m = 0, n = 0, nnz = 0, max_row = 0;
     int32_t vt = SPMV_F64;
     spmv_config cfg{};
+    spmv_config packed_req{};  // configuration the current packs were built for
+    bool packed = false;
     int sm_count = 0;
     // CSR (always present: the base every other format is packed from)
     int32_t *rowptr = nullptr;

@@ -52,8 +52,13 @@ k_csr_vector(int64_t m, const int *__restrict__ rowptr, const int *__restrict__ 
 #pragma unroll
                     for (int u = 0; u < UNROLL; ++u) {
                         const int kk = k + u * TPR;
-                        c[u] = kk < e ? ld_s(colidx + kk) : -1;
-                        v[u] = kk < e ? ld_val(vals + kk) : T(0);
+                        if constexpr (TPR <= 2) {  // lanes walk their own rows: keep lines in L1
+                            c[u] = kk < e ? __ldg(colidx + kk) : -1;
+                            v[u] = kk < e ? ld_val_c(vals + kk) : T(0);
+                        } else {
+                            c[u] = kk < e ? ld_s(colidx + kk) : -1;
+                            v[u] = kk < e ? ld_val(vals + kk) : T(0);
+                        }
                     }
 #pragma unroll
                     for (int u = 0; u < UNROLL; ++u)

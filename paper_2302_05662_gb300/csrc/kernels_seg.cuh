@@ -64,17 +64,29 @@ __device__ __forceinline__ void seg_load(bool full, int64_t a, int cnt, const in
     }
 }
 
-// Inclusive segmented scan over lanes keyed by a nondecreasing row id.
+// Inclusive segmented scan over lanes keyed by a nondecreasing row id.  A
+// step whose add no lane needs (no run of equal keys that long) is skipped
+// by a warp vote, so short rows pay no floating-point adds here.
 template <typename T>
 __device__ __forceinline__ T seg_scan(int key, T val) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
         const int k = __shfl_up_sync(0xffffffffu, key, d);
+        const bool need = lane >= d && k == key;
+        if (!__any_sync(0xffffffffu, need)) break;   // runs are contiguous: longer steps add nothing
         const T v = __shfl_up_sync(0xffffffffu, val, d);
-        if (lane >= d && k == key) val += v;
+        if (need) val += v;
     }
     return val;
+}
+
+// Lane carry: a lane whose first row continues from the previous lane adds
+// that lane's scanned run; the add is issued only if some lane needs it.
+template <typename T>
+__device__ __forceinline__ T seg_carry(bool need, T fs, T pval) {
+    if (__any_sync(0xffffffffu, need)) return need ? fs + pval : fs;
+    return fs;
 }
 
 // ---------------------------------------------------------------------------
@@ -145,8 +157,8 @@ k_coo_seg(int64_t nnz, int64_t m, const int *__restrict__ rows, const int *__res
         const int H = __shfl_sync(0xffffffffu, r[0], 0);
         const int64_t hc0 = meta0[c], tc1 = meta1[c];
         const bool h_back = hc0 < c, t_fwd = tc1 > c;
+        const T total = seg_carry<T>(cnt > 0 && fflush && lane > 0 && pkey == fr, fs, pval);
         if (cnt > 0 && fflush) {
-            const T total = fs + ((lane > 0 && pkey == fr) ? pval : T(0));
             if (fr == H && h_back)  // H started in an earlier chunk and ends in this one
                 seg_arrive<T, ACCUM>(fr, c, hc0, c, total, P, y, ep);
             else
@@ -227,8 +239,8 @@ k_csr_split(int64_t nnz, int64_t m, const int *__restrict__ rowptr, const int *_
         const T pval = __shfl_up_sync(0xffffffffu, sc, 1);
         const int hstart = __ldg(rowptr + H);
         const bool h_back = hstart < E0;
+        const T total = seg_carry<T>(cnt > 0 && fflush && lane > 0 && pkey == fr, fs, pval);
         if (cnt > 0 && fflush) {
-            const T total = fs + ((lane > 0 && pkey == fr) ? pval : T(0));
             if (fr == H && h_back) {
                 const int64_t c0 = hstart / C, c1 = (__ldg(rowptr + H + 1) - 1) / C;
                 seg_arrive<T, false>(fr, c, c0, c1, total, P, y, ep);

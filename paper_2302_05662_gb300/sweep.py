@@ -1,0 +1,182 @@
+"""Exhaustive search over the tuned space: format x kernel/launch parameters.
+
+The paper labels each matrix with the configuration that measured best
+(Section 5.4, Step 2: a dataset of diverse matrices run under many
+configurations) and learns to predict it.  This module times every point of
+the space on the GPU through the C ABI: CUDA-event timing on the launching
+stream, the L2 flushed between repetitions, median of the repetitions.
+Results go to a JSON-lines file, one record per (matrix, configuration);
+a rerun skips records already present (checkpoint/resume).
+
+The space (Section 4 knobs 1-4, plus threads per row and unroll):
+  CSR  threads_per_row in {1,2,4,8,16,32} or the nnz-balanced split,
+  ELL, COO, HYB, BSR (r in {2, 4}),
+  each at threads_per_block in {32, 64, 128, 256, 512, 1024}.
+The register cap, unroll and L1/shared carveout are refined on the winner.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import time
+
+import numpy as np
+
+from . import binding as B
+
+TPB = (32, 64, 128, 256, 512, 1024)
+CSR_TPR = (1, 2, 4, 8, 16, 32, B.TPR_SPLIT)
+
+
+def label_space(tpb=TPB):
+    """The selector's label space: (format, threads_per_block, threads_per_row)
+    points, each a dict of spmv_config fields."""
+    out = []
+    for t in tpb:
+        for tpr in CSR_TPR:
+            out.append(dict(format=B.FMT_CSR, threads_per_block=t, threads_per_row=tpr))
+        out.append(dict(format=B.FMT_ELL, threads_per_block=t))
+        out.append(dict(format=B.FMT_COO, threads_per_block=t))
+        out.append(dict(format=B.FMT_HYB, threads_per_block=t))
+        for s in (1, 4):
+            out.append(dict(format=B.FMT_BSR, threads_per_block=t, threads_per_row=s, bsr_block=4))
+    return out
+
+
+def refine_space(best: dict):
+    """Register cap x unroll x carveout around a winning point."""
+    out = []
+    for rc in (32, 64):
+        for u in (1, 2, 4):
+            for cv in (-1, 0, 100):
+                d = dict(best)
+                d.update(regcap=rc, unroll=u, carveout=cv)
+                out.append(d)
+    return out
+
+
+def config_key(d: dict) -> str:
+    return ",".join(f"{k}={d[k]}" for k in sorted(d))
+
+
+class Timer:
+    """Times spmv_run on one handle with CUDA events, flushing L2 between
+    repetitions by writing a buffer twice the L2 size."""
+
+    def __init__(self, l2_bytes: int = 129 * 2**20):
+        import torch
+        self.torch = torch
+        self.flush_buf = torch.empty(2 * l2_bytes // 4, dtype=torch.int32, device="cuda")
+
+    def time_us(self, h, x, y, reps: int = 7, warm: int = 2) -> float:
+        torch = self.torch
+        stream = torch.cuda.current_stream()
+        for _ in range(warm):
+            B.spmv_run(h, 1.0, x, 0.0, y, stream.cuda_stream)
+        ts = []
+        for _ in range(reps):
+            self.flush_buf.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            B.spmv_run(h, 1.0, x, 0.0, y, stream.cuda_stream)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e3)
+        return statistics.median(ts)
+
+
+def device_matrix(coo, value_dtype="f64"):
+    import torch
+    from . import matgen
+    rows = torch.from_numpy(coo.rows).cuda()
+    cols = torch.from_numpy(coo.cols).cuda()
+    if value_dtype == "bf16":
+        bits = matgen.bf16_bits(matgen.round_to_bf16(coo.vals)).view(np.int16)
+        vals = torch.from_numpy(bits).cuda().view(torch.bfloat16)
+    else:
+        vals = torch.from_numpy(coo.vals).cuda().to(torch.float64 if value_dtype == "f64" else torch.float32)
+    return rows, cols, vals
+
+
+def sweep_matrix(coo, space, timer: Timer, reps=7, value_dtype="f64", seed=0):
+    """Time every configuration of `space` on one matrix.  Returns a list of
+    (config dict, median microseconds or None when the format is refused)."""
+    import torch
+    rows, cols, vals = device_matrix(coo, value_dtype)
+    xdt = torch.float64 if value_dtype == "f64" else torch.float32
+    x = torch.from_numpy(np.random.default_rng(seed).uniform(-1, 1, coo.n)).to(xdt).cuda()
+    y = torch.zeros(coo.m, dtype=xdt, device="cuda")
+    h = B.spmv_create(coo.m, coo.n, rows, cols, vals)
+    out = []
+    try:
+        for cfg in space:
+            try:
+                B.spmv_set_config(h, B.make_config(**cfg))
+            except B.SpmvError:
+                out.append((cfg, None))
+                continue
+            out.append((cfg, timer.time_us(h, x, y, reps=reps)))
+    finally:
+        B.spmv_destroy(h)
+    return out
+
+
+def default_csr(coo) -> dict:
+    """The 'default CSR' baseline: CSR with the library's default threads per
+    row and 256 threads per block."""
+    return dict(format=B.FMT_CSR, threads_per_block=256, threads_per_row=0)
+
+
+def generate_dataset_matrix(idx: int, n_lo=1e3, n_hi=2.1e6):
+    """Matrix idx of the selector dataset: family by index, n log-uniform in
+    [n_lo, n_hi] from the matrix seed, family parameters jittered."""
+    from . import matgen
+    rng = np.random.default_rng(10_000 + idx)
+    fam = matgen.FAMILIES[idx % len(matgen.FAMILIES)]
+    n = int(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi))))
+    return fam, matgen.family_matrix(fam, n, seed=20_000 + idx, jitter=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description="exhaustive format/launch sweep")
+    ap.add_argument("--start", type=int, default=0)
+    ap.add_argument("--count", type=int, default=10)
+    ap.add_argument("--out", required=True)
+    ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--n-hi", type=float, default=2.1e6)
+    ap.add_argument("--time-budget", type=float, default=1e9, help="seconds; stop cleanly after")
+    args = ap.parse_args()
+    from . import build
+    build.build()
+    B.load_library()
+    done = set()
+    if os.path.exists(args.out):
+        with open(args.out) as fh:
+            for line in fh:
+                try:
+                    done.add(json.loads(line)["matrix"])
+                except Exception:
+                    pass
+    timer = Timer()
+    space = label_space()
+    t0 = time.time()
+    with open(args.out, "a") as fh:
+        for idx in range(args.start, args.start + args.count):
+            if idx in done:
+                continue
+            if time.time() - t0 > args.time_budget:
+                break
+            fam, coo = generate_dataset_matrix(idx, n_hi=args.n_hi)
+            res = sweep_matrix(coo, space, timer, reps=args.reps, seed=idx)
+            rec = {"matrix": idx, "family": fam, "m": coo.m, "n": coo.n, "nnz": coo.nnz,
+                   "times": [[config_key(c), t] for c, t in res]}
+            fh.write(json.dumps(rec) + "\n")
+            fh.flush()
+
+
+if __name__ == "__main__":
+    main()
