@@ -199,6 +199,51 @@ SPMV_API int spmv_export_bytes(spmv_handle h, int32_t array_id, int64_t *bytes);
 SPMV_API int spmv_export(spmv_handle h, int32_t array_id, void *d_dst, int64_t bytes,
                 void *stream);
 
+/*
+ * Largest nnz spmv_coo_run_noalloc accepts (2^25).  Its scratch is one fixed
+ * device array of about 4.5 MiB, compiled into the library, that every GPU
+ * which loads the library holds until the process exits.
+ */
+#define SPMV_NOALLOC_MAX_NNZ 33554432
+
+/*
+ * y <- alpha * A * x + beta * y for a matrix given as COO triplets sorted by
+ * row, without allocating any device memory.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc -- code
+ * running inside another library's memory pool or callback, real-time or
+ * embedded code that may not allocate after start-up, or processes whose
+ * device allocator is exhausted or off limits.  It runs the segmented-
+ * reduction COO kernel straight on the caller's arrays and keeps the
+ * kernel's scratch (per-chunk metadata, partial row sums, arrival counters
+ * and exchange slots) in the library's fixed device array instead of in
+ * allocated memory.
+ *
+ * d_rows, d_cols, d_vals hold nnz triplets with rows in nondecreasing order
+ * (columns in any order; repeated pairs are summed), values of value_type;
+ * d_x has n entries and d_y m entries (double for SPMV_F64, else float).
+ * All arrays stay owned by the caller.  beta == 0 means y is not read.
+ *
+ * Errors: SPMV_ERR_UNSUPPORTED when nnz > SPMV_NOALLOC_MAX_NNZ or m, n >=
+ * 2^31; SPMV_ERR_INVALID for bad sizes, NULL arrays, or triplets that are
+ * out of range or not sorted by row (checked on the device before any
+ * product is formed; y is then left unchanged); SPMV_ERR_CUDA.
+ *
+ * The call synchronises `stream` once, to read that check.  The first call
+ * on a device does the set-up: it looks up the device address of the fixed
+ * array on that device (once per device, with the device current), and the
+ * CUDA driver loads the library's kernels then if it has not yet done so;
+ * make that first call before any stream capture.  Later calls allocate
+ * nothing.  Every call shares the one array, and each call
+ * clears the parts that must start at zero, so calls are correct one after
+ * another; calls whose kernels overlap on the GPU (other threads, other
+ * streams) race on the array and give wrong results.
+ */
+SPMV_API int spmv_coo_run_noalloc(int64_t m, int64_t n, int64_t nnz,
+                                  const int32_t *d_rows, const int32_t *d_cols,
+                                  const void *d_vals, int32_t value_type,
+                                  double alpha, const void *d_x, double beta,
+                                  void *d_y, void *stream);
+
 /* Frees every device array of the handle.  NULL is accepted. */
 SPMV_API int spmv_destroy(spmv_handle h);
 

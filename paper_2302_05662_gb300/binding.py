@@ -27,7 +27,7 @@ TPR_SPLIT = -1
 # every entry point include/spmv.h declares (checked by the CPU test suite)
 EXPORTED = ("spmv_config_default", "spmv_create", "spmv_set_config", "spmv_get_config",
             "spmv_get_info", "spmv_run", "spmv_export_bytes", "spmv_export", "spmv_destroy",
-            "spmv_last_error")
+            "spmv_last_error", "spmv_coo_run_noalloc")
 
 
 class SpmvError(RuntimeError):
@@ -85,6 +85,8 @@ def load_library(path: str | None = None):
         "spmv_export_bytes": (ctypes.c_int, [_VP, _I32, ctypes.POINTER(_I64)]),
         "spmv_export": (ctypes.c_int, [_VP, _I32, _VP, _I64, _VP]),
         "spmv_destroy": (ctypes.c_int, [_VP]),
+        "spmv_coo_run_noalloc": (ctypes.c_int, [_I64, _I64, _I64, _VP, _VP, _VP, _I32, _D, _VP, _D, _VP,
+                                                _VP]),
         "spmv_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -173,6 +175,18 @@ def spmv_export(h: int, array_id: int, out, stream=None):
     """Copy an internal array into the device tensor `out` (exact size)."""
     nbytes = out.numel() * out.element_size()
     _check(load_library().spmv_export(h, int(array_id), _ptr(out), nbytes, _stream(stream)))
+
+
+NOALLOC_MAX_NNZ = 1 << 25
+
+
+def spmv_coo_run_noalloc(m: int, n: int, rows, cols, vals, alpha: float, x, beta: float, y, stream=None):
+    """y <- alpha*A*x + beta*y from row-sorted device COO triplets, with no
+    device allocation (the library's fixed scratch array is used)."""
+    nnz = int(rows.numel()) if rows is not None else 0
+    _check(load_library().spmv_coo_run_noalloc(int(m), int(n), nnz, _ptr(rows), _ptr(cols), _ptr(vals),
+                                               value_type_of(vals.dtype), float(alpha), _ptr(x), float(beta),
+                                               _ptr(y), _stream(stream)))
 
 
 def spmv_destroy(h: int):
