@@ -1,14 +1,15 @@
 """Benchmark: the SpMV format sweep on one GB300 (or N independent replicas).
 
-One step = y <- alpha*A*x + beta*y (alpha = 1, beta = 0) once for every
-(matrix, kernel variant) pair of the format sweep: five synthetic matrices
-(27-point stencil 128^3, Poisson(16) random rows n = 2^20, R-MAT scale 20
-edge factor 16, banded n = 2^20 half-width 32, block-diagonal 4x4 n = 2^20)
-times six kernels (vector CSR, split CSR, ELL, COO, HYB, BSR), fp64 values
-and vectors with int32 indices.  value = 2 * (sum of nnz over the pairs) per
-step / step time, in GFLOP/s.  Every step streams several GB, far more than
-the 129 MB L2, and launches are ordered variant-major so that a kernel's
-matrix has been evicted by the kernels launched in between.
+Workload: the format sweep over five synthetic matrices (27-point stencil
+128^3, Poisson(16) random rows n = 2^20, R-MAT scale 20 edge factor 16,
+banded n = 2^20 half-width 32, block-diagonal 4x4 n = 2^20), fp64 values and
+vectors, int32 indices.  For each matrix the exhaustive sweep over format x
+launch parameters is run first (the judge of the selector; its per-format
+best times are reported in format_sweep), then the trained selector picks a
+configuration on the device (spmv_select).  One timed step = one product
+y <- A x of every matrix in its selected configuration; value = 2 * (sum of
+nnz) per step / step time, in GFLOP/s.  Every step streams ~2 GB, far more
+than the 129 MB L2, and consecutive launches use different matrices.
 
 --impl reference times the fp64 CPU oracle instead (the timed baseline of
 this method; there is no other reference implementation).
@@ -39,7 +40,7 @@ THROTTLE_BITS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_p
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=400)
+    p.add_argument("--steps", type=int, default=2000)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16"])
@@ -47,7 +48,10 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=20)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--only", default=None, help="comma-separated matrix names (profiling runs)")
-    p.add_argument("--kernels", default=None, help="comma-separated kernel variants (profiling runs)")
+    p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--fixed", default=None,
+                   help="profiling runs: skip tuning and selection, run this kernel variant's default "
+                        "configuration (csr, csr_split, ell, coo, hyb, bsr)")
     return p.parse_args()
 
 
@@ -168,7 +172,7 @@ def reference_arm(args, rank):
     value = flops * args.steps / dt / 1e9
     sample = (f"per step: first rows holding <= {budget} nonzeros of each of the five "
               f"matrices ({flops // 2} nonzeros), one fp64 oracle product each")
-    line = {"impl": "reference", "metric": "SpMV GFLOP/s (format sweep, 5 matrices x 6 kernels)",
+    line = {"impl": "reference", "metric": "SpMV GFLOP/s (selected format+config per matrix, 5 format-sweep matrices)",
             "value": round(value, 4), "unit": "GFLOP/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -181,10 +185,11 @@ def reference_arm(args, rank):
 
 
 def workload_config(args):
-    return {"workload": "format sweep: stencil27 128^3, poisson16 2^20, rmat s20 ef16, banded 2^20 w32, "
-                        "blockdiag4 2^20; kernels csr, csr_split, ell, coo, hyb, bsr",
+    return {"workload": "format sweep over stencil27 128^3, poisson16 2^20, rmat s20 ef16, banded 2^20 w32, "
+                        "blockdiag4 2^20 (CSR/ELL/COO/HYB/BSR x launch parameters); step = one product per "
+                        "matrix in the configuration the selector picks",
             "scale": args.scale, "value_dtype": args.dtype, "index_dtype": "int32", "alpha": 1.0, "beta": 0.0,
-            "l2": "inputs larger than L2: each step streams several GB; launches are variant-major"}
+            "l2": "inputs larger than L2: each step streams ~2 GB; consecutive launches use different matrices"}
 
 
 def cpu_baseline(mats_host):
@@ -211,13 +216,108 @@ def cpu_baseline(mats_host):
                       f"3 fp64 oracle products each"}
 
 
+NAMES = ("stencil27_128^3", "poisson16_2^20", "rmat_s20_ef16", "banded_2^20_w32", "blockdiag4_2^20")
+FMT_KEYS = {0: "csr", 1: "ell", 2: "coo", 3: "hyb", 4: "bsr"}
+
+
+def fmt_name(cfg: dict) -> str:
+    n = FMT_KEYS[cfg["format"]]
+    return "csr_split" if n == "csr" and cfg.get("threads_per_row") == -1 else n
+
+
+def tune_matrix(B, sweep, h, coo, x, y, timer, reps):
+    """Exhaustive search on one handle: the label space, then register cap x
+    unroll x carveout around the winner.  Returns (best cfg, best us,
+    per-format best {name: (cfg, us)})."""
+    space = sweep.label_space()
+    times = []
+    for cfg in space:
+        try:
+            B.spmv_set_config(h, B.make_config(**cfg))
+        except B.SpmvError:
+            continue
+        times.append((cfg, timer.time_us(h, x, y, reps=reps)))
+    per_fmt = {}
+    for cfg, t in times:
+        k = fmt_name(cfg)
+        if k not in per_fmt or t < per_fmt[k][1]:
+            per_fmt[k] = (cfg, t)
+    best_cfg, best_t = min(times, key=lambda ct: ct[1])
+    for cfg in sweep.refine_space(best_cfg):
+        try:
+            B.spmv_set_config(h, B.make_config(**cfg))
+        except B.SpmvError:
+            continue
+        t = timer.time_us(h, x, y, reps=reps)
+        if t < best_t:
+            best_cfg, best_t = cfg, t
+    return best_cfg, best_t, per_fmt
+
+
+def batched_section(B, matgen, torch, count=512, seed=7, steps=20):
+    """512 uneven fp32 matrices: one graph-captured persistent launch (after
+    the autotuner) against one spmv_run per matrix."""
+    import math
+    rng = np.random.default_rng(seed)
+    hs, xs, ys, nnz = [], [], [], 0
+    for i in range(count):
+        fam = matgen.FAMILIES[i % len(matgen.FAMILIES)]
+        n = int(math.exp(rng.uniform(math.log(1e3), math.log(2e5))))
+        coo = matgen.family_matrix(fam, n, seed=5000 + i, jitter=True)
+        r = torch.from_numpy(coo.rows).cuda()
+        c = torch.from_numpy(coo.cols).cuda()
+        v = torch.from_numpy(coo.vals).cuda().float()
+        hs.append(B.spmv_create(coo.m, coo.n, r, c, v))
+        xs.append(torch.from_numpy(matgen.dense_vector(coo.n, 9000 + i)).float().cuda())
+        ys.append(torch.zeros(coo.m, dtype=torch.float32, device="cuda"))
+        nnz += coo.nnz
+    ones, zeros = np.ones(count), np.zeros(count)
+    b = B.spmv_batch_create(hs, ones, xs, zeros, ys)
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    try:
+        B.spmv_batch_tune(b)
+        modes, items, tpb = B.spmv_batch_get_plan(b, count)
+
+        def timed(fn):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / steps
+
+        t_graph = timed(lambda: B.spmv_batch_launch(b, sh))
+
+        def separate():
+            for k in range(count):
+                B.spmv_run(hs[k], 1.0, xs[k], 0.0, ys[k], sh)
+        t_sep = timed(separate)
+    finally:
+        B.spmv_batch_destroy(b)
+        for h in hs:
+            B.spmv_destroy(h)
+    return {"matrices": count, "nnz": nnz, "value_dtype": "f32",
+            "graph_ms": round(t_graph, 4), "graph_gflops": round(2 * nnz / (t_graph * 1e-3) / 1e9, 2),
+            "separate_launches_ms": round(t_sep, 4),
+            "separate_gflops": round(2 * nnz / (t_sep * 1e-3) / 1e9, 2),
+            "speedup": round(t_sep / t_graph, 3),
+            "plan": {"items": items, "threads_per_block": tpb,
+                     "split_matrices": int((modes == 0).sum()),
+                     "vector_matrices": int((modes != 0).sum())}}
+
+
 def ours(args, world, rank, local):
     import torch
     import torch.distributed as dist
     from paper_2302_05662_gb300 import binding as B
     from paper_2302_05662_gb300 import build as build_mod
-    from paper_2302_05662_gb300 import matgen
-    from paper_2302_05662_gb300.workload import SWEEP_VARIANTS
+    from paper_2302_05662_gb300 import matgen, replicas, sweep
+    from paper_2302_05662_gb300 import selector as S
 
     torch.cuda.set_device(local)
     if rank == 0 or world == 1:
@@ -226,55 +326,64 @@ def ours(args, world, rank, local):
         dist.barrier()
     B.load_library()
     vt = {"f64": B.SPMV_F64, "f32": B.SPMV_F32, "bf16": B.SPMV_BF16}[args.dtype]
-    vdt = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[args.dtype]
     xdt = torch.float64 if vt == B.SPMV_F64 else torch.float32
     vsz = {"f64": 8, "f32": 4, "bf16": 2}[args.dtype]
     xsz = 8 if vt == B.SPMV_F64 else 4
+    have_selector = os.path.exists(S.DEFAULT_BLOB)
+    if have_selector:
+        S.load_default_selector()
+    timer = sweep.Timer()
 
-    pairs = []           # (variant, matrix, handle, x, y, nnz, bytes, launches)
-    skipped = []
-    mats_host = []
-    mats_info = {}
-    names_all = [n for n in ("stencil27_128^3", "poisson16_2^20", "rmat_s20_ef16", "banded_2^20_w32",
-                             "blockdiag4_2^20")]
     only = set(args.only.split(",")) if args.only else None
-    kern_only = set(args.kernels.split(",")) if args.kernels else None
+    mats = []          # per matrix: name, handle, x, y, nnz, bytes, chosen cfg
+    mats_host = []
+    format_sweep = []
+    selector_rows = []
     for mname, coo in matgen.workload_matrices(args.scale, only=only):
-        k = names_all.index(mname) if mname in names_all else len(mats_info)
+        k = NAMES.index(mname) if mname in NAMES else len(mats)
         x_np = matgen.dense_vector(coo.n, 100 + k)
         mats_host.append((mname, coo, x_np))
-        rows = torch.from_numpy(coo.rows).cuda()
-        cols = torch.from_numpy(coo.cols).cuda()
-        if vt == B.SPMV_BF16:
-            bits = matgen.bf16_bits(matgen.round_to_bf16(coo.vals)).view(np.int16)
-            vals = torch.from_numpy(bits).cuda().view(torch.bfloat16)
-        else:
-            vals = torch.from_numpy(coo.vals).cuda().to(vdt)
-        x = torch.from_numpy(x_np).cuda().to(xdt)
-        mats_info[mname] = {"m": coo.m, "n": coo.n, "nnz": coo.nnz}
-        for vname, kw in SWEEP_VARIANTS:
-            if kern_only is not None and vname not in kern_only:
-                continue
-            try:
-                h = B.spmv_create(coo.m, coo.n, rows, cols, vals, B.make_config(**kw))
-            except B.SpmvError as e:
-                skipped.append({"matrix": mname, "kernel": vname, "why": str(e)[:160]})
-                continue
-            info = B.spmv_get_info(h)
-            y = torch.zeros(coo.m, dtype=xdt, device="cuda")
-            launches = 2 if (info.format == B.FMT_HYB and info.hyb_coo_nnz > 0) else 1
-            pairs.append({"variant": vname, "matrix": mname, "h": h, "x": x, "y": y, "nnz": info.nnz,
-                          "bytes": byte_model(coo.m, coo.n, info.nnz, vsz, xsz),
-                          "format_bytes": info.format_bytes, "launches": launches})
+        rows, cols, vals = sweep.device_matrix(coo, args.dtype)
+        x = torch.from_numpy(x_np).to(xdt).cuda()
+        y = torch.zeros(coo.m, dtype=xdt, device="cuda")
+        h = B.spmv_create(coo.m, coo.n, rows, cols, vals)
         del rows, cols, vals
+        nnz = B.spmv_get_info(h).nnz
+        nbytes = byte_model(coo.m, coo.n, nnz, vsz, xsz)
+        if args.fixed:
+            from paper_2302_05662_gb300.workload import SWEEP_VARIANTS
+            fixed = dict(dict(SWEEP_VARIANTS)[args.fixed])
+            B.spmv_set_config(h, B.make_config(**fixed))
+            t = timer.time_us(h, x, y, reps=3)
+            best_cfg, best_t, per_fmt = fixed, t, {fmt_name(fixed): (fixed, t)}
+        else:
+            best_cfg, best_t, per_fmt = tune_matrix(B, sweep, h, coo, x, y, timer, reps=5)
+        for fname, (cfg, t) in sorted(per_fmt.items()):
+            gbs = nbytes / (t * 1e-6) / 1e9
+            format_sweep.append({"matrix": mname, "kernel": fname, "config": cfg, "us": round(t, 2),
+                                 "gflops": round(2 * nnz / (t * 1e-6) / 1e9, 1), "gbs": round(gbs, 1)})
+        chosen, source = best_cfg, ("fixed" if args.fixed else "exhaustive")
+        if have_selector and not args.fixed:
+            sel_cfg, _ = B.spmv_select(h)
+            B.spmv_set_config(h, sel_cfg)
+            t_sel = timer.time_us(h, x, y, reps=5)
+            chosen = {kk: getattr(sel_cfg, kk) for kk, _ in sel_cfg._fields_}
+            source = "selector"
+            selector_rows.append({"matrix": mname, "selected": fmt_name(chosen), "selected_us": round(t_sel, 2),
+                                  "best": fmt_name(best_cfg), "best_us": round(best_t, 2),
+                                  "slowdown": round(t_sel / best_t, 4)})
+        else:
+            B.spmv_set_config(h, B.make_config(**best_cfg))
+        info = B.spmv_get_info(h)
+        mats.append({"matrix": mname, "h": h, "x": x, "y": y, "nnz": nnz, "bytes": nbytes, "cfg": chosen,
+                     "source": source, "best_us": best_t,
+                     "launches": (2 if info.format == B.FMT_HYB and info.hyb_coo_nnz > 0 else 1)})
     torch.cuda.synchronize()
-    order = {v: i for i, (v, _) in enumerate(SWEEP_VARIANTS)}
-    pairs.sort(key=lambda p: (order[p["variant"]], list(mats_info).index(p["matrix"])))
     stream = torch.cuda.current_stream()
     sh = stream.cuda_stream
 
     def step(events=None):
-        for i, p in enumerate(pairs):
+        for i, p in enumerate(mats):
             if events is not None:
                 events[i][0].record(stream)
             B.spmv_run(p["h"], 1.0, p["x"], 0.0, p["y"], sh)
@@ -284,43 +393,40 @@ def ours(args, world, rank, local):
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
-
-    # --- device-timed region: inputs resident in HBM
-    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in pairs] for _ in range(args.steps)]
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in mats]
+          for _ in range(args.steps)]
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
-    gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0] or 0) \
-        if os.environ.get("CUDA_VISIBLE_DEVICES", "").replace(",", "").isdigit() else local
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    gpu_index = int(vis.split(",")[local]) if vis.replace(",", "").isdigit() else local
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(gpu_index) as clk:
+        torch.cuda.nvtx.range_push("timed_step")    # ncu --nvtx-include "timed_step/"
         t_start.record(stream)
-        for s in range(args.steps):
-            step(ev[s])
+        for s_ in range(args.steps):
+            step(ev[s_])
         t_end.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     if world > 1:
         dist.barrier()
     elapsed_ms = t_start.elapsed_time(t_end)
-    per_pair_ms = [statistics.mean(ev[s][i][0].elapsed_time(ev[s][i][1]) for s in range(args.steps))
-                   for i in range(len(pairs))]
-    if world > 1:
-        t = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    flops_step = sum(2 * p["nnz"] for p in pairs)
-    value = flops_step * args.steps * world / (elapsed_ms * 1e-3) / 1e9
+    per_ms = [statistics.mean(ev[s_][i][0].elapsed_time(ev[s_][i][1]) for s_ in range(args.steps))
+              for i in range(len(mats))]
+    elapsed_ms = replicas.max_over_ranks(elapsed_ms, device="cuda")
+    flops_step = sum(2 * p["nnz"] for p in mats)
+    value = replicas.whole_job_rate(flops_step, args.steps, world, elapsed_ms) / 1e9
 
-    # --- end to end through the C ABI: x from pinned host memory, y back
-    xs_host = [p["x"].cpu().pin_memory() for p in pairs]
-    ys_host = [torch.empty(p["y"].numel(), dtype=xdt).pin_memory() for p in pairs]
+    # end to end through the C ABI: x from pinned host memory, y back to it
+    xs_host = [p["x"].cpu().pin_memory() for p in mats]
+    ys_host = [torch.empty(p["y"].numel(), dtype=xdt).pin_memory() for p in mats]
     h2d = sum(t.numel() * t.element_size() for t in xs_host)
     d2h = sum(t.numel() * t.element_size() for t in ys_host)
 
     def e2e_step():
-        for i, p in enumerate(pairs):
+        for i, p in enumerate(mats):
             p["x"].copy_(xs_host[i], non_blocking=True)
             B.spmv_run(p["h"], 1.0, p["x"], 0.0, p["y"], sh)
             ys_host[i].copy_(p["y"], non_blocking=True)
@@ -337,53 +443,56 @@ def ours(args, world, rank, local):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = flops_step * args.e2e_steps * world / (e2e_ms * 1e-3) / 1e9
+    e2e_ms = replicas.max_over_ranks(e2e_ms, device="cuda")
+    e2e_value = replicas.whole_job_rate(flops_step, args.e2e_steps, world, e2e_ms) / 1e9
 
-    # --- roofline of the dominant kernel (largest share of the step)
     peak, peak_kind = measured_peak()
     per_kernel = []
-    for p, ms in zip(pairs, per_pair_ms):
+    for p, ms in zip(mats, per_ms):
         gbs = p["bytes"] / (ms * 1e-3) / 1e9
-        per_kernel.append({"matrix": p["matrix"], "kernel": p["variant"], "us": round(ms * 1e3, 2),
-                           "gflops": round(2 * p["nnz"] / (ms * 1e-3) / 1e9, 2), "gbs": round(gbs, 1),
-                           "frac": round(gbs / peak, 4),
-                           "format_gbs": round(p["format_bytes"] / (ms * 1e-3) / 1e9, 1)})
-    dom = max(range(len(pairs)), key=lambda i: per_pair_ms[i])
-    dp = pairs[dom]
-    achieved = dp["bytes"] / (per_pair_ms[dom] * 1e-3) / 1e9
+        per_kernel.append({"matrix": p["matrix"], "kernel": fmt_name(p["cfg"]), "config": p["cfg"],
+                           "source": p["source"], "us": round(ms * 1e3, 2),
+                           "gflops": round(2 * p["nnz"] / (ms * 1e-3) / 1e9, 1), "gbs": round(gbs, 1),
+                           "frac": round(gbs / peak, 4)})
+    dom = max(range(len(mats)), key=lambda i: per_ms[i])
+    dp = mats[dom]
+    achieved = dp["bytes"] / (per_ms[dom] * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": None,
-                "kernel": f"{dp['variant']} on {dp['matrix']}",
-                "algorithmic_bytes_per_launch": dp["bytes"], "peak_source": peak_kind}
-    best = {}
-    for pk in per_kernel:
-        if pk["matrix"] not in best or pk["frac"] > best[pk["matrix"]]["frac"]:
-            best[pk["matrix"]] = pk
+                "kernel": f"{fmt_name(dp['cfg'])} on {dp['matrix']}",
+                "algorithmic_bytes_per_launch": dp["bytes"], "peak_source": peak_kind,
+                "time_share": round(per_ms[dom] / sum(per_ms), 3)}
+    for fs in format_sweep:
+        fs["frac"] = round(fs["gbs"] / peak, 4)
     clocks = clk.summary()
+    batched = None
+    if not args.no_batched and only is None and not args.fixed:
+        batched = batched_section(B, matgen, torch)
     if rank != 0:
+        for p in mats:
+            B.spmv_destroy(p["h"])
         return
     cpu = None if args.no_cpu_baseline else cpu_baseline(mats_host)
     cfg = workload_config(args)
     cfg["parallelism"] = f"replicas{world}" if world > 1 else "single"
-    cfg["matrices"] = mats_info
-    cfg["skipped"] = skipped
-    line = {"metric": "SpMV GFLOP/s (format sweep, 5 matrices x 6 kernels)", "value": round(value, 2),
-            "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": round(elapsed_ms / args.steps, 4), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": args.dtype, "data": "synthetic", "config": cfg,
+    cfg["matrices"] = {p["matrix"]: p["nnz"] for p in mats}
+    sel_summary = None
+    if selector_rows:
+        sl = np.array([r["slowdown"] for r in selector_rows])
+        sel_summary = {"per_matrix": selector_rows, "geomean_slowdown": round(float(np.exp(np.mean(np.log(sl)))), 4),
+                       "within_10pct": float(np.mean(sl <= 1.10))}
+    line = {"metric": "SpMV GFLOP/s (selected format+config per matrix, 5 format-sweep matrices)",
+            "value": round(value, 2), "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(elapsed_ms / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic", "config": cfg,
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": round(e2e_value, 2), "unit": "GFLOP/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "clocks": clocks, "gpu_launches": sum(p["launches"] for p in pairs) * args.steps,
-            "best_per_matrix": {m: {"kernel": v["kernel"], "gflops": v["gflops"], "frac": v["frac"]}
-                                for m, v in best.items()},
-            "per_kernel": per_kernel}
+            "clocks": clocks, "gpu_launches": sum(p["launches"] for p in mats) * args.steps,
+            "per_kernel": per_kernel, "selector": sel_summary, "format_sweep": format_sweep,
+            "batched": batched}
     print(json.dumps(line), flush=True)
-    for p in pairs:
+    for p in mats:
         B.spmv_destroy(p["h"])
 
 

@@ -133,7 +133,8 @@ SPMV_API void spmv_config_default(spmv_config *cfg, int32_t format);
  * Errors: SPMV_ERR_INVALID for negative sizes, a NULL array with nnz > 0,
  * or any triplet outside [0,m) x [0,n) (checked on the device);
  * SPMV_ERR_UNSUPPORTED for m, n or nnz >= 2^31 or a format whose padded
- * size exceeds the limit (ELL); SPMV_ERR_OOM; SPMV_ERR_CUDA.
+ * storage exceeds 8 nnz + 2^24 value slots (ELL width x rows; BSR blocks x
+ * r^2); SPMV_ERR_OOM; SPMV_ERR_CUDA.
  * Synchronises `stream`.
  */
 SPMV_API int spmv_create(spmv_handle *out, int64_t m, int64_t n, int64_t nnz,
@@ -243,6 +244,99 @@ SPMV_API int spmv_coo_run_noalloc(int64_t m, int64_t n, int64_t nnz,
                                   const void *d_vals, int32_t value_type,
                                   double alpha, const void *d_x, double beta,
                                   void *d_y, void *stream);
+
+/* Number of sparsity features spmv_features / spmv_select produce. */
+#define SPMV_NUM_FEATURES 20
+
+/*
+ * Sparsity features of the handle's matrix (Section 5.5, Table 2, plus the
+ * selector's structural extras), computed on the device from the CSR
+ * arrays and copied to h_out[SPMV_NUM_FEATURES] (host), in this order:
+ *   0 n (rows)  1 nnz  2 density nnz/(m n)  3 mean row length (Avg_nnz)
+ *   4 population variance of row lengths (Var_nnz)  5 its square root
+ *   (Std_nnz)  6 min  7 max row length  8 median (lower middle)  9 mode
+ *   (smallest on ties)  10 ELL_ratio nnz/(m max)  11 Gini coefficient of
+ *   row lengths  12 coefficient of variation  13 fraction of empty rows
+ *   14 bandwidth max|i-j|  15 mean |i-j|  16 fraction of diagonal entries
+ *   17 4x4 block fill nnz/(16 blocks)  18 2x2 block fill  19 fraction of
+ *   nonzeros beyond the HYB ELL width.
+ * Ratios with a zero denominator are 0.  Synchronises `stream`.
+ */
+SPMV_API int spmv_features(spmv_handle h, double *h_out, void *stream);
+
+/*
+ * Load the selector: a 2-layer MLP classifier (Section 5.4: one classifier
+ * mapping features to the best configuration) for the current device.
+ * h_blob holds `count` floats: magic 2302, version 1, F (= 20), H, K; then
+ * mu[F], sigma[F] (input standardisation after log1p of the count-like
+ * features 0,1,3-9,14,15), W1[H][F], b1[H], W2[K][H], b2[K]; then K label
+ * configurations of 8 values each (the spmv_config fields in order).
+ * H <= 256, K <= 512.  Copies the weights to the device.  A NULL blob with
+ * count 0 unloads the selector.  Errors: SPMV_ERR_INVALID for a malformed
+ * blob.
+ */
+SPMV_API int spmv_selector_load(const float *h_blob, int64_t count);
+
+/*
+ * Run the selector's fused inference kernel on host features (20 doubles):
+ * writes the chosen class to *choice and, when h_logits is not NULL, the K
+ * output logits (fp32).  Synchronises `stream`.  SPMV_ERR_INVALID if no
+ * selector is loaded on the current device.
+ */
+SPMV_API int spmv_selector_infer(const double *h_features, float *h_logits,
+                                 int32_t *choice, void *stream);
+
+/*
+ * Pick the format and kernel parameters for the handle's matrix (Section
+ * 5.3 steps 1-2): features on the device, then the loaded selector's fused
+ * inference kernel; *out_cfg receives the chosen label configuration, or
+ * the default CSR configuration when no selector is loaded.  The features
+ * are also copied to h_features (may be NULL).  Does not change the handle;
+ * apply the choice with spmv_set_config.  Synchronises `stream`.
+ */
+SPMV_API int spmv_select(spmv_handle h, spmv_config *out_cfg, double *h_features,
+                         void *stream);
+
+/*
+ * Batched SpMV (a batch of independent products y_i <- alpha_i A_i x_i +
+ * beta_i y_i in one persistent launch).  The paper runs one kernel per
+ * matrix; a batch of hundreds of uneven matrices would then pay one launch
+ * each.  A batch plan holds, for every matrix, a mode -- nonzero chunks of
+ * 32*items entries per warp (split) or 32-row groups with 1..32 lanes per
+ * row (vector) -- and a list of warp work items over all matrices that a
+ * grid of resident thread blocks consumes through one atomic counter.  The
+ * counter reset and the kernel are captured in a CUDA graph.
+ *
+ * spmv_batch_create: hs[i] (all of one value type), alpha[i], beta[i] (host
+ * arrays) and device vectors d_x[i] (n_i entries), d_y[i] (m_i entries), i <
+ * count.  The plan reads the handles' CSR arrays: the handles and vectors
+ * must outlive the plan and keep their addresses.  Default modes come from
+ * row-length statistics.  Synchronises `stream`.
+ * spmv_batch_tune: autotuner -- times every mode per matrix on one-matrix
+ * launches, then the chunk size (items 4/8/16) and block size
+ * (128/256/512) on the whole batch, keeps the fastest and re-captures the
+ * graph.  Overwrites y.  Synchronises `stream`.
+ * spmv_batch_launch: replays the graph on `stream` (no synchronisation).
+ * spmv_batch_get_plan: copies the per-matrix modes (0 = split, else lanes
+ * per row; h_modes may be NULL), the items and the block size.
+ * spmv_batch_run: create + launch + destroy in one call (synchronises).
+ * Errors: SPMV_ERR_INVALID (NULL arrays or handles, mixed value types),
+ * SPMV_ERR_OOM, SPMV_ERR_CUDA.
+ */
+typedef struct spmv_batch *spmv_batch_handle;
+
+SPMV_API int spmv_batch_create(spmv_batch_handle *out, const spmv_handle *hs,
+                               int32_t count, const double *alpha,
+                               const void *const *d_x, const double *beta,
+                               void *const *d_y, void *stream);
+SPMV_API int spmv_batch_tune(spmv_batch_handle b, void *stream);
+SPMV_API int spmv_batch_launch(spmv_batch_handle b, void *stream);
+SPMV_API int spmv_batch_get_plan(spmv_batch_handle b, int32_t *h_modes,
+                                 int32_t *items, int32_t *threads_per_block);
+SPMV_API int spmv_batch_destroy(spmv_batch_handle b);
+SPMV_API int spmv_batch_run(const spmv_handle *hs, int32_t count,
+                            const double *alpha, const void *const *d_x,
+                            const double *beta, void *const *d_y, void *stream);
 
 /* Frees every device array of the handle.  NULL is accepted. */
 SPMV_API int spmv_destroy(spmv_handle h);

@@ -27,7 +27,9 @@ TPR_SPLIT = -1
 # every entry point include/spmv.h declares (checked by the CPU test suite)
 EXPORTED = ("spmv_config_default", "spmv_create", "spmv_set_config", "spmv_get_config",
             "spmv_get_info", "spmv_run", "spmv_export_bytes", "spmv_export", "spmv_destroy",
-            "spmv_last_error", "spmv_coo_run_noalloc")
+            "spmv_last_error", "spmv_coo_run_noalloc", "spmv_features", "spmv_selector_load",
+            "spmv_selector_infer", "spmv_select", "spmv_batch_create", "spmv_batch_tune",
+            "spmv_batch_launch", "spmv_batch_get_plan", "spmv_batch_destroy", "spmv_batch_run")
 
 
 class SpmvError(RuntimeError):
@@ -85,6 +87,16 @@ def load_library(path: str | None = None):
         "spmv_export_bytes": (ctypes.c_int, [_VP, _I32, ctypes.POINTER(_I64)]),
         "spmv_export": (ctypes.c_int, [_VP, _I32, _VP, _I64, _VP]),
         "spmv_destroy": (ctypes.c_int, [_VP]),
+        "spmv_batch_create": (ctypes.c_int, [ctypes.POINTER(_VP), _VP, _I32, _VP, _VP, _VP, _VP, _VP]),
+        "spmv_batch_tune": (ctypes.c_int, [_VP, _VP]),
+        "spmv_batch_launch": (ctypes.c_int, [_VP, _VP]),
+        "spmv_batch_get_plan": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
+        "spmv_batch_destroy": (ctypes.c_int, [_VP]),
+        "spmv_batch_run": (ctypes.c_int, [_VP, _I32, _VP, _VP, _VP, _VP, _VP]),
+        "spmv_features": (ctypes.c_int, [_VP, _VP, _VP]),
+        "spmv_selector_load": (ctypes.c_int, [_VP, _I64]),
+        "spmv_selector_infer": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(_I32), _VP]),
+        "spmv_select": (ctypes.c_int, [_VP, ctypes.POINTER(spmv_config), _VP, _VP]),
         "spmv_coo_run_noalloc": (ctypes.c_int, [_I64, _I64, _I64, _VP, _VP, _VP, _I32, _D, _VP, _D, _VP,
                                                 _VP]),
         "spmv_last_error": (ctypes.c_char_p, []),
@@ -175,6 +187,95 @@ def spmv_export(h: int, array_id: int, out, stream=None):
     """Copy an internal array into the device tensor `out` (exact size)."""
     nbytes = out.numel() * out.element_size()
     _check(load_library().spmv_export(h, int(array_id), _ptr(out), nbytes, _stream(stream)))
+
+
+NUM_FEATURES = 20
+
+
+def spmv_features(h: int, stream=None):
+    """The 20 sparsity features of the handle's matrix (numpy float64)."""
+    import numpy as np
+    out = np.zeros(NUM_FEATURES, dtype=np.float64)
+    _check(load_library().spmv_features(h, out.ctypes.data, _stream(stream)))
+    return out
+
+
+def spmv_selector_load(blob):
+    """Load a selector blob (sequence of float32) on the current device."""
+    import numpy as np
+    b = np.ascontiguousarray(blob, dtype=np.float32)
+    _check(load_library().spmv_selector_load(b.ctypes.data, int(b.size)))
+
+
+def spmv_selector_unload():
+    """Unload the selector on the current device (spmv_selector_load(NULL, 0))."""
+    _check(load_library().spmv_selector_load(None, 0))
+
+
+def spmv_selector_infer(features, k: int, stream=None):
+    """(choice, logits[k]) of the loaded selector for host features."""
+    import numpy as np
+    f = np.ascontiguousarray(features, dtype=np.float64)
+    logits = np.zeros(k, dtype=np.float32)
+    c = _I32()
+    _check(load_library().spmv_selector_infer(f.ctypes.data, logits.ctypes.data, ctypes.byref(c),
+                                              _stream(stream)))
+    return c.value, logits
+
+
+def spmv_select(h: int, stream=None):
+    """(chosen spmv_config, features) for the handle's matrix."""
+    import numpy as np
+    cfg = spmv_config()
+    f = np.zeros(NUM_FEATURES, dtype=np.float64)
+    _check(load_library().spmv_select(h, ctypes.byref(cfg), f.ctypes.data, _stream(stream)))
+    return cfg, f
+
+
+def _batch_arrays(handles, alphas, xs, betas, ys):
+    import numpy as np
+    n = len(handles)
+    hs = (_VP * n)(*handles)
+    al = np.ascontiguousarray(alphas, dtype=np.float64)
+    be = np.ascontiguousarray(betas, dtype=np.float64)
+    xp = (_VP * n)(*[_ptr(x) for x in xs])
+    yp = (_VP * n)(*[_ptr(y) for y in ys])
+    return n, hs, al, be, xp, yp
+
+
+def spmv_batch_create(handles, alphas, xs, betas, ys, stream=None) -> int:
+    """Batch plan over handles with device vectors xs, ys (torch tensors)."""
+    n, hs, al, be, xp, yp = _batch_arrays(handles, alphas, xs, betas, ys)
+    b = _VP()
+    _check(load_library().spmv_batch_create(ctypes.byref(b), hs, n, al.ctypes.data, xp, be.ctypes.data, yp,
+                                            _stream(stream)))
+    return b.value
+
+
+def spmv_batch_tune(b: int, stream=None):
+    _check(load_library().spmv_batch_tune(b, _stream(stream)))
+
+
+def spmv_batch_launch(b: int, stream=None):
+    _check(load_library().spmv_batch_launch(b, _stream(stream)))
+
+
+def spmv_batch_get_plan(b: int, count: int):
+    import numpy as np
+    modes = np.zeros(count, dtype=np.int32)
+    it, tpb = _I32(), _I32()
+    _check(load_library().spmv_batch_get_plan(b, modes.ctypes.data, ctypes.byref(it), ctypes.byref(tpb)))
+    return modes, it.value, tpb.value
+
+
+def spmv_batch_destroy(b: int):
+    if b:
+        _check(load_library().spmv_batch_destroy(b))
+
+
+def spmv_batch_run(handles, alphas, xs, betas, ys, stream=None):
+    n, hs, al, be, xp, yp = _batch_arrays(handles, alphas, xs, betas, ys)
+    _check(load_library().spmv_batch_run(hs, n, al.ctypes.data, xp, be.ctypes.data, yp, _stream(stream)))
 
 
 NOALLOC_MAX_NNZ = 1 << 25

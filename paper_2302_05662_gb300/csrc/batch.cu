@@ -1,0 +1,441 @@
+// Batched SpMV: hundreds of uneven matrices in one persistent launch.
+//
+// Each matrix contributes work items for one warp each: chunks of 32*ITEMS
+// nonzeros (split mode, for power-law or very short rows) or groups of 32
+// rows with a per-matrix number of lanes per row (vector mode).  A grid of
+// resident thread blocks pulls items from one atomic counter, so small and
+// large matrices share the GPU without a launch per matrix.  The counter
+// reset and the kernel are captured once in a CUDA graph and replayed.  An
+// autotuner times the per-matrix mode and the batch-wide chunk and block
+// sizes (the paper's compile-time parameters of Section 4, chosen per
+// matrix by measurement instead of by a model).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "launch.cuh"
+
+struct spmv_batch {
+    int count = 0, vt = SPMV_F64, items = 8, tpb = 256, sm_count = 0;
+    std::vector<spmv_handle> hs;
+    std::vector<double> alpha, beta;
+    std::vector<const void *> x;
+    std::vector<void *> y;
+    std::vector<int> modes;  // 0 split, else threads per row
+    // device state
+    void *d_mats = nullptr;
+    int64_t *d_item_off = nullptr;
+    int64_t total_items = 0;
+    std::vector<int32_t *> metas;
+    spmv::Partials part;
+    unsigned long long *d_counter = nullptr;
+    cudaStream_t cs = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace spmv {
+namespace {
+
+struct BatchMat {
+    const int *rowptr;
+    const int *colidx;
+    const void *vals;
+    const void *x;
+    void *y;
+    double alpha, beta;
+    int64_t m, nnz;
+    int64_t part_off;  // first chunk of this matrix in the batch partials
+    const int *meta0;  // split: row of each chunk's first entry
+    int mode;          // 0 split, else lanes per row
+    int pad;
+};
+
+template <typename V, typename T, int ITEMS>
+__global__ void __launch_bounds__(512)
+k_batch(const BatchMat *__restrict__ mats, int count, const int64_t *__restrict__ item_off, int64_t total,
+        unsigned long long *counter, const PartialsT<T> P) {
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(counter, 1ull);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= (unsigned long long)total) break;
+        int lo = 0, hi = count - 1;  // matrix owning the item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if ((unsigned long long)__ldg(item_off + mid) <= item) lo = mid; else hi = mid - 1;
+        }
+        const BatchMat M = mats[lo];
+        const int64_t local = (int64_t)item - __ldg(item_off + lo);
+        const Epi<T> ep((T)M.alpha, (T)M.beta);
+        const V *vals = (const V *)M.vals;
+        const T *x = (const T *)M.x;
+        T *y = (T *)M.y;
+        if (M.mode == 0) {
+            PartialsT<T> Pm = P;
+            Pm.head += M.part_off;
+            Pm.tail += M.part_off;
+            Pm.count += M.part_off;
+            Pm.xslot += M.part_off;
+            csr_split_chunk<V, T, ITEMS>(local, M.nnz, M.m, M.rowptr, M.colidx, vals, x, y, ep, M.meta0, Pm);
+        } else {
+            const int64_t base = local * 32;
+            const int big = 0x7fffffff;
+            switch (M.mode) {
+            case 1: csr_vector_rows<V, T, 1, 2>(base, M.m, M.rowptr, M.colidx, vals, x, y, ep, big); break;
+            case 2: csr_vector_rows<V, T, 2, 2>(base, M.m, M.rowptr, M.colidx, vals, x, y, ep, big); break;
+            case 4: csr_vector_rows<V, T, 4, 2>(base, M.m, M.rowptr, M.colidx, vals, x, y, ep, big); break;
+            case 8: csr_vector_rows<V, T, 8, 2>(base, M.m, M.rowptr, M.colidx, vals, x, y, ep, big); break;
+            case 16: csr_vector_rows<V, T, 16, 2>(base, M.m, M.rowptr, M.colidx, vals, x, y, ep, big); break;
+            default: csr_vector_rows<V, T, 32, 2>(base, M.m, M.rowptr, M.colidx, vals, x, y, ep, big); break;
+            }
+        }
+    }
+}
+
+template <typename V, typename T, int ITEMS>
+int launch_batch_t(const spmv_batch *b, const BatchMat *mats, int count, const int64_t *item_off, int64_t total,
+                   cudaStream_t s) {
+    auto kern = k_batch<V, T, ITEMS>;
+    const int per_sm = resident_blocks((const void *)kern, b->tpb);
+    const int64_t need = (total + b->tpb / 32 - 1) / (b->tpb / 32);
+    const int64_t cap = (int64_t)per_sm * b->sm_count;
+    const int grid = (int)std::max<int64_t>(1, std::min(need, cap));
+    kern<<<grid, b->tpb, 0, s>>>(mats, count, item_off, total, b->d_counter, PartialsT<T>::of(b->part));
+    SPMV_CUDA_TRY(cudaGetLastError());
+    return SPMV_OK;
+}
+
+template <int VT>
+int launch_batch_vt(const spmv_batch *b, const BatchMat *mats, int count, const int64_t *item_off, int64_t total,
+                    cudaStream_t s) {
+    using V = typename VT_<VT>::V;
+    using T = typename VT_<VT>::T;
+    switch (b->items) {
+    case 4: return launch_batch_t<V, T, 4>(b, mats, count, item_off, total, s);
+    case 16: return launch_batch_t<V, T, 16>(b, mats, count, item_off, total, s);
+    default: return launch_batch_t<V, T, 8>(b, mats, count, item_off, total, s);
+    }
+}
+
+// counter reset + one persistent kernel over `count` descriptors
+int launch_batch(const spmv_batch *b, const BatchMat *mats, int count, const int64_t *item_off, int64_t total,
+                 cudaStream_t s) {
+    SPMV_CUDA_TRY(cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), s));
+    if (total == 0) return SPMV_OK;
+    switch (b->vt) {
+    case SPMV_F64: return launch_batch_vt<SPMV_F64>(b, mats, count, item_off, total, s);
+    case SPMV_F32: return launch_batch_vt<SPMV_F32>(b, mats, count, item_off, total, s);
+    default: return launch_batch_vt<SPMV_BF16>(b, mats, count, item_off, total, s);
+    }
+}
+
+int default_mode(const spmv_matrix *h) {
+    if (h->nnz == 0 || h->m == 0) return 1;  // vector mode writes y = beta*y for every row
+    const double mean = (double)h->nnz / (double)h->m;
+    if ((double)h->max_row > 8.0 * mean + 64.0 || mean < 2.0) return 0;
+    int t = 1;
+    while (t < 32 && 2.0 * t <= mean / 8.0) t *= 2;
+    return t;
+}
+
+void free_device(spmv_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    if (b->d_mats) cudaFree(b->d_mats);
+    if (b->d_item_off) cudaFree(b->d_item_off);
+    b->d_mats = nullptr;
+    b->d_item_off = nullptr;
+    for (int32_t *p : b->metas)
+        if (p) cudaFree(p);
+    b->metas.clear();
+    free_partials(&b->part);
+}
+
+// Builds descriptors, item offsets, split metadata and partials for the
+// current modes / items, then captures the graph.
+int build(spmv_batch *b, cudaStream_t s) {
+    free_device(b);
+    const int C = 32 * b->items;
+    std::vector<BatchMat> mats(b->count);
+    std::vector<int64_t> off(b->count + 1, 0);
+    b->metas.assign(b->count, nullptr);
+    int64_t chunks_total = 0;
+    for (int i = 0; i < b->count; ++i) {
+        const spmv_matrix *h = b->hs[i];
+        BatchMat &M = mats[i];
+        M.rowptr = h->rowptr;
+        M.colidx = h->colidx;
+        M.vals = h->vals;
+        M.x = b->x[i];
+        M.y = b->y[i];
+        M.alpha = b->alpha[i];
+        M.beta = b->beta[i];
+        M.m = h->m;
+        M.nnz = h->nnz;
+        M.mode = b->modes[i];
+        M.part_off = 0;
+        M.meta0 = nullptr;
+        M.pad = 0;
+        int64_t items;
+        if (M.mode == 0) {
+            const int64_t nch = (h->nnz + C - 1) / C;
+            SPMV_CUDA_TRY(cudaMalloc((void **)&b->metas[i], sizeof(int32_t) * (nch + 1)));
+            SPMV_TRY(build_split_meta(h->rowptr, h->m, h->nnz, C, b->metas[i], s));
+            M.meta0 = b->metas[i];
+            M.part_off = chunks_total;
+            chunks_total += nch;
+            items = nch;
+        } else {
+            items = (h->m + 31) / 32;
+        }
+        off[i + 1] = off[i] + items;
+    }
+    b->total_items = off[b->count];
+    SPMV_TRY(alloc_partials(&b->part, chunks_total, 1, b->vt, s));
+    SPMV_CUDA_TRY(cudaMalloc(&b->d_mats, sizeof(BatchMat) * std::max(1, b->count)));
+    SPMV_CUDA_TRY(cudaMalloc((void **)&b->d_item_off, sizeof(int64_t) * (b->count + 1)));
+    SPMV_CUDA_TRY(cudaMemcpyAsync(b->d_mats, mats.data(), sizeof(BatchMat) * b->count, cudaMemcpyHostToDevice, s));
+    SPMV_CUDA_TRY(cudaMemcpyAsync(b->d_item_off, off.data(), sizeof(int64_t) * (b->count + 1),
+                                  cudaMemcpyHostToDevice, s));
+    SPMV_CUDA_TRY(cudaStreamSynchronize(s));
+    // capture: counter reset + kernel, replayed by spmv_batch_launch
+    SPMV_CUDA_TRY(cudaStreamBeginCapture(b->cs, cudaStreamCaptureModeThreadLocal));
+    int st = launch_batch(b, (const BatchMat *)b->d_mats, b->count, b->d_item_off, b->total_items, b->cs);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->cs, &g);
+    if (st != SPMV_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_status(e, "cudaStreamEndCapture");
+    b->graph = g;
+    SPMV_CUDA_TRY(cudaGraphInstantiate(&b->exec, g, 0));
+    return SPMV_OK;
+}
+
+// median time (us) of `reps` launches of a sub-batch on stream s
+float time_launch(const spmv_batch *b, const BatchMat *mats, int count, const int64_t *off, int64_t total,
+                  cudaStream_t s, int reps, int *status) {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    std::vector<float> ts;
+    *status = launch_batch(b, mats, count, off, total, s);  // warm-up
+    for (int r = 0; r < reps && *status == SPMV_OK; ++r) {
+        cudaEventRecord(e0, s);
+        *status = launch_batch(b, mats, count, off, total, s);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ts.push_back(ms * 1e3f);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (ts.empty()) return 1e30f;
+    std::sort(ts.begin(), ts.end());
+    return ts[ts.size() / 2];
+}
+
+}  // namespace
+}  // namespace spmv
+
+using namespace spmv;
+
+extern "C" {
+
+int spmv_batch_create(spmv_batch_handle *out, const spmv_handle *hs, int32_t count, const double *alpha,
+                      const void *const *d_x, const double *beta, void *const *d_y, void *stream) {
+    if (!out || count < 0 || (count > 0 && (!hs || !alpha || !d_x || !beta || !d_y))) {
+        set_error("spmv_batch_create: bad arguments");
+        return SPMV_ERR_INVALID;
+    }
+    *out = nullptr;
+    int vt = -1;
+    for (int i = 0; i < count; ++i) {
+        if (!hs[i]) {
+            set_error("spmv_batch_create: NULL handle %d", i);
+            return SPMV_ERR_INVALID;
+        }
+        if (vt >= 0 && hs[i]->vt != vt) {
+            set_error("spmv_batch_create: handles mix value types");
+            return SPMV_ERR_INVALID;
+        }
+        vt = hs[i]->vt;
+        if ((hs[i]->m > 0 && !d_y[i]) || (hs[i]->nnz > 0 && !d_x[i])) {
+            set_error("spmv_batch_create: NULL vector for matrix %d", i);
+            return SPMV_ERR_INVALID;
+        }
+    }
+    spmv_batch *b = new (std::nothrow) spmv_batch();
+    if (!b) {
+        set_error("spmv_batch_create: host allocation failed");
+        return SPMV_ERR_OOM;
+    }
+    b->count = count;
+    b->vt = vt < 0 ? SPMV_F64 : vt;
+    b->hs.assign(hs, hs + count);
+    b->alpha.assign(alpha, alpha + count);
+    b->beta.assign(beta, beta + count);
+    b->x.assign(d_x, d_x + count);
+    b->y.assign(d_y, d_y + count);
+    b->modes.resize(count);
+    for (int i = 0; i < count; ++i) b->modes[i] = default_mode(hs[i]);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_counter, sizeof(unsigned long long));
+    int st = e == cudaSuccess ? SPMV_OK : cuda_status(e, "spmv_batch_create");
+    if (st == SPMV_OK) st = build(b, (cudaStream_t)stream);
+    if (st != SPMV_OK) {
+        free_device(b);
+        if (b->d_counter) cudaFree(b->d_counter);
+        if (b->cs) cudaStreamDestroy(b->cs);
+        delete b;
+        return st;
+    }
+    *out = b;
+    return SPMV_OK;
+}
+
+int spmv_batch_launch(spmv_batch_handle b, void *stream) {
+    if (!b) {
+        set_error("spmv_batch_launch: NULL batch");
+        return SPMV_ERR_INVALID;
+    }
+    SPMV_CUDA_TRY(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+    return SPMV_OK;
+}
+
+int spmv_batch_tune(spmv_batch_handle b, void *stream) {
+    if (!b) {
+        set_error("spmv_batch_tune: NULL batch");
+        return SPMV_ERR_INVALID;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int cand[7] = {0, 1, 2, 4, 8, 16, 32};
+    // 1) per matrix: time each mode on a one-matrix sub-batch
+    for (int i = 0; i < b->count; ++i) {
+        const spmv_matrix *h = b->hs[i];
+        if (h->m == 0) continue;
+        int best_mode = b->modes[i];
+        float best_t = 1e30f;
+        for (int mode : cand) {
+            if (mode == 0 && h->nnz == 0) continue;
+            b->modes[i] = mode;
+            spmv_batch one;  // a view of matrix i only (shares the counter, no graph)
+            one.count = 1;
+            one.vt = b->vt;
+            one.items = b->items;
+            one.tpb = b->tpb;
+            one.sm_count = b->sm_count;
+            one.hs = {b->hs[i]};
+            one.alpha = {b->alpha[i]};
+            one.beta = {b->beta[i]};
+            one.x = {b->x[i]};
+            one.y = {b->y[i]};
+            one.modes = {mode};
+            one.d_counter = b->d_counter;
+            one.cs = b->cs;
+            // build descriptors without capturing a graph
+            const int C = 32 * one.items;
+            BatchMat M{h->rowptr, h->colidx, h->vals, b->x[i], b->y[i], b->alpha[i], b->beta[i], h->m, h->nnz, 0,
+                       nullptr, mode, 0};
+            int64_t off[2] = {0, mode == 0 ? (h->nnz + C - 1) / C : (h->m + 31) / 32};
+            int32_t *meta = nullptr;
+            BatchMat *d_m = nullptr;
+            int64_t *d_off = nullptr;
+            int st = SPMV_OK;
+            if (mode == 0) {
+                if (cudaMalloc((void **)&meta, sizeof(int32_t) * (off[1] + 1)) != cudaSuccess) st = SPMV_ERR_OOM;
+                if (st == SPMV_OK) st = build_split_meta(h->rowptr, h->m, h->nnz, C, meta, s);
+                M.meta0 = meta;
+                if (st == SPMV_OK) st = alloc_partials(&one.part, off[1], 1, one.vt, s);
+            }
+            if (st == SPMV_OK && (cudaMalloc((void **)&d_m, sizeof(BatchMat)) != cudaSuccess ||
+                                  cudaMalloc((void **)&d_off, sizeof(off)) != cudaSuccess))
+                st = SPMV_ERR_OOM;
+            if (st == SPMV_OK) {
+                cudaMemcpyAsync(d_m, &M, sizeof(M), cudaMemcpyHostToDevice, s);
+                cudaMemcpyAsync(d_off, off, sizeof(off), cudaMemcpyHostToDevice, s);
+                const float t = time_launch(&one, d_m, 1, d_off, off[1], s, 3, &st);
+                if (st == SPMV_OK && t < best_t) {
+                    best_t = t;
+                    best_mode = mode;
+                }
+            }
+            free_partials(&one.part);
+            if (meta) cudaFree(meta);
+            if (d_m) cudaFree(d_m);
+            if (d_off) cudaFree(d_off);
+            one.d_counter = nullptr;
+            one.cs = nullptr;
+            if (st != SPMV_OK) return st;
+        }
+        b->modes[i] = best_mode;
+    }
+    // 2) batch-wide: chunk size and block size on the whole batch
+    int best_items = b->items, best_tpb = b->tpb;
+    float best_t = 1e30f;
+    for (int items : {4, 8, 16}) {
+        for (int tpb : {128, 256, 512}) {
+            b->items = items;
+            b->tpb = tpb;
+            SPMV_TRY(build(b, s));
+            int st = SPMV_OK;
+            const float t = time_launch(b, (const BatchMat *)b->d_mats, b->count, b->d_item_off, b->total_items, s,
+                                        5, &st);
+            SPMV_TRY(st);
+            if (t < best_t) {
+                best_t = t;
+                best_items = items;
+                best_tpb = tpb;
+            }
+        }
+    }
+    b->items = best_items;
+    b->tpb = best_tpb;
+    return build(b, s);
+}
+
+int spmv_batch_get_plan(spmv_batch_handle b, int32_t *h_modes, int32_t *items, int32_t *threads_per_block) {
+    if (!b) {
+        set_error("spmv_batch_get_plan: NULL batch");
+        return SPMV_ERR_INVALID;
+    }
+    if (h_modes)
+        for (int i = 0; i < b->count; ++i) h_modes[i] = b->modes[i];
+    if (items) *items = b->items;
+    if (threads_per_block) *threads_per_block = b->tpb;
+    return SPMV_OK;
+}
+
+int spmv_batch_destroy(spmv_batch_handle b) {
+    if (!b) return SPMV_OK;
+    if (b->cs) cudaStreamSynchronize(b->cs);
+    free_device(b);
+    if (b->d_counter) cudaFree(b->d_counter);
+    if (b->cs) cudaStreamDestroy(b->cs);
+    delete b;
+    return SPMV_OK;
+}
+
+int spmv_batch_run(const spmv_handle *hs, int32_t count, const double *alpha, const void *const *d_x,
+                   const double *beta, void *const *d_y, void *stream) {
+    spmv_batch_handle b = nullptr;
+    SPMV_TRY(spmv_batch_create(&b, hs, count, alpha, d_x, beta, d_y, stream));
+    int st = spmv_batch_launch(b, stream);
+    if (st == SPMV_OK) {
+        cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+        if (e != cudaSuccess) st = cuda_status(e, "spmv_batch_run");
+    }
+    spmv_batch_destroy(b);
+    return st;
+}
+
+}  // extern "C"

@@ -812,6 +812,10 @@ int pack_bsr(spmv_matrix *h, int r, cudaStream_t s) {
     int64_t nblk = 0;
     SPMV_TRY(exclusive_scan(head.p, pos.p, nnz, s, &nblk));
     h->bsr_blocks = nblk;
+    if ((double)nblk * r * r > 8.0 * (double)nnz + (double)(1 << 24)) {
+        set_error("BSR: %lld blocks of %dx%d exceed 8 x nnz + 2^24 value slots", (long long)nblk, r, r);
+        return SPMV_ERR_UNSUPPORTED;
+    }
     SPMV_TRY(dalloc(&h->bsr_col, (size_t)nblk));
     SPMV_TRY(dalloc_bytes(&h->bsr_val, vs * nblk * r * r));
     SPMV_CUDA_TRY(cudaMemsetAsync(h->bsr_val, 0, vs * nblk * r * r, s));
@@ -835,6 +839,14 @@ int pack_bsr(spmv_matrix *h, int r, cudaStream_t s) {
 }
 
 }  // namespace
+
+int build_split_meta(const int32_t *rowptr, int64_t m, int64_t nnz, int C, int32_t *meta0, cudaStream_t s) {
+    const int64_t nchunks = (nnz + C - 1) / C;
+    if (m == 0) return SPMV_OK;
+    k_seg_meta_split<<<grid1d(nchunks + 1, 256), 256, 0, s>>>(rowptr, m, nnz, C, nchunks, meta0);
+    SPMV_CUDA_TRY(cudaGetLastError());
+    return SPMV_OK;
+}
 
 int ensure_seg_scratch(spmv_matrix *h, int items, bool split_csr, cudaStream_t s) {
     SegScratch &g = h->seg;

@@ -288,6 +288,7 @@ void free_packed(spmv_matrix *h);
 int expand_rows(const int32_t *rowptr, int64_t m, int64_t nnz, int32_t *rows_out,
                 cudaStream_t s);
 int ensure_seg_scratch(spmv_matrix *h, int items, bool split_csr, cudaStream_t s);
+int build_split_meta(const int32_t *rowptr, int64_t m, int64_t nnz, int C, int32_t *meta0, cudaStream_t s);
 int alloc_partials(Partials *p, int64_t units, int stride, int vt, cudaStream_t s);
 void free_partials(Partials *p);
 int build_long_rows(spmv_matrix *h, const int32_t *rowptr, int64_t nrows, int64_t threshold, int64_t seg,

@@ -22,54 +22,62 @@ constexpr unsigned FULLMASK = 0xffffffffu;
 // long_threshold are left to k_csr_long.  All loops are warp-uniform, so the
 // shuffle reduction always has every lane.
 // ---------------------------------------------------------------------------
+// Rows [base, base + 32) with TPR lanes per row; the whole warp calls it.
+template <typename V, typename T, int TPR, int UNROLL>
+__device__ __forceinline__ void csr_vector_rows(int64_t base, int64_t m, const int *__restrict__ rowptr,
+                                                const int *__restrict__ colidx, const V *__restrict__ vals,
+                                                const T *__restrict__ x, T *__restrict__ y, const Epi<T> &ep,
+                                                int long_threshold) {
+    constexpr int RPW = 32 / TPR;  // rows per warp per step
+    const int lane = threadIdx.x & 31;
+    const int sub = lane % TPR, grp = lane / TPR;
+    const int64_t rr = base + lane;
+    const int my_s = rr < m ? __ldg(rowptr + rr) : 0;
+    const int my_e = rr < m ? __ldg(rowptr + rr + 1) : 0;
+#pragma unroll 1
+    for (int g = 0; g < TPR; ++g) {
+        const int src = g * RPW + grp;
+        const int s = __shfl_sync(FULLMASK, my_s, src);
+        const int e = __shfl_sync(FULLMASK, my_e, src);
+        const int64_t row = base + src;
+        const bool skip = row >= m || e - s > long_threshold;
+        T acc = T(0);
+        if (!skip) {
+            for (int k = s + sub; k < e; k += TPR * UNROLL) {
+                int c[UNROLL];
+                T v[UNROLL];
+#pragma unroll
+                for (int u = 0; u < UNROLL; ++u) {
+                    const int kk = k + u * TPR;
+                    if constexpr (TPR <= 2) {  // lanes walk their own rows: keep lines in L1
+                        c[u] = kk < e ? __ldg(colidx + kk) : -1;
+                        v[u] = kk < e ? ld_val_c(vals + kk) : T(0);
+                    } else {
+                        c[u] = kk < e ? ld_s(colidx + kk) : -1;
+                        v[u] = kk < e ? ld_val(vals + kk) : T(0);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < UNROLL; ++u)
+                    if (c[u] >= 0) acc += v[u] * ld_x(x, c[u]);
+            }
+        }
+#pragma unroll
+        for (int off = TPR / 2; off > 0; off >>= 1) acc += __shfl_down_sync(FULLMASK, acc, off, TPR);
+        if (sub == 0 && !skip) ep.store(y, row, acc);
+    }
+}
+
 template <typename V, typename T, int TPR, int UNROLL, int REGCAP>
 __global__ void __launch_bounds__(1024) __maxnreg__(REGCAP)
 k_csr_vector(int64_t m, const int *__restrict__ rowptr, const int *__restrict__ colidx,
              const V *__restrict__ vals, const T *__restrict__ x, T *__restrict__ y, T alpha, T beta,
              int long_threshold) {
     const Epi<T> ep(alpha, beta);
-    constexpr int RPW = 32 / TPR;  // rows per warp per step
-    const int lane = threadIdx.x & 31;
-    const int sub = lane % TPR, grp = lane / TPR;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t base = warp * 32; base < m; base += nwarps * 32) {
-        const int64_t rr = base + lane;
-        const int my_s = rr < m ? __ldg(rowptr + rr) : 0;
-        const int my_e = rr < m ? __ldg(rowptr + rr + 1) : 0;
-#pragma unroll 1
-        for (int g = 0; g < TPR; ++g) {
-            const int src = g * RPW + grp;
-            const int s = __shfl_sync(FULLMASK, my_s, src);
-            const int e = __shfl_sync(FULLMASK, my_e, src);
-            const int64_t row = base + src;
-            const bool skip = row >= m || e - s > long_threshold;
-            T acc = T(0);
-            if (!skip) {
-                for (int k = s + sub; k < e; k += TPR * UNROLL) {
-                    int c[UNROLL];
-                    T v[UNROLL];
-#pragma unroll
-                    for (int u = 0; u < UNROLL; ++u) {
-                        const int kk = k + u * TPR;
-                        if constexpr (TPR <= 2) {  // lanes walk their own rows: keep lines in L1
-                            c[u] = kk < e ? __ldg(colidx + kk) : -1;
-                            v[u] = kk < e ? ld_val_c(vals + kk) : T(0);
-                        } else {
-                            c[u] = kk < e ? ld_s(colidx + kk) : -1;
-                            v[u] = kk < e ? ld_val(vals + kk) : T(0);
-                        }
-                    }
-#pragma unroll
-                    for (int u = 0; u < UNROLL; ++u)
-                        if (c[u] >= 0) acc += v[u] * ld_x(x, c[u]);
-                }
-            }
-#pragma unroll
-            for (int off = TPR / 2; off > 0; off >>= 1) acc += __shfl_down_sync(FULLMASK, acc, off, TPR);
-            if (sub == 0 && !skip) ep.store(y, row, acc);
-        }
-    }
+    for (int64_t base = warp * 32; base < m; base += nwarps * 32)
+        csr_vector_rows<V, T, TPR, UNROLL>(base, m, rowptr, colidx, vals, x, y, ep, long_threshold);
 }
 
 // Long CSR rows: one thread block per segment of a long row; segments of one

@@ -176,7 +176,94 @@ k_coo_seg(int64_t nnz, int64_t m, const int *__restrict__ rows, const int *__res
 // Split CSR: chunks of C nonzeros; meta0[c] = row holding entry c*C,
 // meta0[nchunks] = m-1.  Lanes find their start row by binary search in the
 // row pointers and walk them, so empty rows are written on the way.
+// csr_split_chunk processes chunk c with the whole warp; k_csr_split runs
+// it over all chunks, the batched kernel over its work list.
 // ---------------------------------------------------------------------------
+template <typename V, typename T, int ITEMS>
+__device__ __forceinline__ void csr_split_chunk(int64_t c, int64_t nnz, int64_t m, const int *__restrict__ rowptr,
+                                                const int *__restrict__ cols, const V *__restrict__ vals,
+                                                const T *__restrict__ x, T *__restrict__ y, const Epi<T> &ep,
+                                                const int *__restrict__ meta0, const PartialsT<T> &P) {
+    constexpr int C = 32 * ITEMS;
+    const int lane = threadIdx.x & 31;
+    const int64_t E0 = c * C, E1 = (E0 + C < nnz) ? E0 + C : nnz;
+    const int64_t a = E0 + (int64_t)lane * ITEMS;
+    const int cnt = E1 - a <= 0 ? 0 : (E1 - a >= ITEMS ? ITEMS : (int)(E1 - a));
+    const int last_lane = (int)((E1 - E0 - 1) / ITEMS);
+    int r_unused[ITEMS];
+    T v[ITEMS], xv[ITEMS];
+    seg_load<V, T, ITEMS, false>(E1 - E0 == C, a, cnt, nullptr, cols, vals, x, r_unused, v, xv);
+    const int H = __ldg(meta0 + c);
+    // Row pointers rowptr[H .. H+32] of the chunk's first rows, staged per
+    // warp in shared memory with one coalesced load: the start-row search
+    // and the walk over short or empty rows read them from there.
+    __shared__ int s_win[32][33];
+    int *win = s_win[threadIdx.x >> 5];
+    __syncwarp();  // the previous chunk's reads of the window are done
+    if ((int64_t)H + lane <= m) win[lane] = __ldg(rowptr + H + lane);
+    if (lane == 0 && (int64_t)H + 32 <= m) win[32] = __ldg(rowptr + H + 32);
+    __syncwarp();
+    auto rp = [&](int64_t r) -> int { return r - H <= 32 ? win[r - H] : __ldg(rowptr + r); };
+    int cur = 0;
+    if (cnt > 0 && a > 0) {  // largest row r in [H, H_next] with rowptr[r] <= a
+        int lo = H, hi = __ldg(meta0 + c + 1);
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (rp(mid) <= a) lo = mid; else hi = mid - 1;
+        }
+        cur = lo;
+    }
+    const int fr = cur;
+    int next_end = cnt > 0 ? rp(cur + 1) : 0;
+    T fs = T(0), acc = T(0);
+    bool fflush = false;
+    if (cnt > 0) {
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            if (j < cnt) {
+                while (a + j >= next_end) {
+                    if (!fflush) { fs = acc; fflush = true; }
+                    else seg_write<T, false>(y, cur, acc, ep);
+                    acc = T(0);
+                    ++cur;
+                    next_end = rp(cur + 1);
+                }
+                acc = fma(v[j], xv[j], acc);
+            }
+        }
+        const int64_t b = a + cnt;
+        while (cur < m && next_end <= b) {
+            if (!fflush) { fs = acc; fflush = true; }
+            else seg_write<T, false>(y, cur, acc, ep);
+            acc = T(0);
+            ++cur;
+            if (cur < m) next_end = rp(cur + 1);
+        }
+    }
+    const int key = (cnt > 0 && cur < m) ? cur : -1;
+    const T sc = seg_scan<T>(key, key >= 0 ? acc : T(0));
+    const int pkey = __shfl_up_sync(0xffffffffu, key, 1);
+    const T pval = __shfl_up_sync(0xffffffffu, sc, 1);
+    const int hstart = rp(H);
+    const bool h_back = hstart < E0;
+    const T total = seg_carry<T>(cnt > 0 && fflush && lane > 0 && pkey == fr, fs, pval);
+    if (cnt > 0 && fflush) {
+        if (fr == H && h_back) {
+            const int64_t c0 = hstart / C, c1 = (rp(H + 1) - 1) / C;
+            seg_arrive<T, false>(fr, c, c0, c1, total, P, y, ep);
+        } else {
+            seg_write<T, false>(y, fr, total, ep);
+        }
+    }
+    if (lane == last_lane && cur < m) {
+        const int s0 = rp(cur);
+        if (s0 < E1 && next_end > E1) {  // open row continues into the next chunk
+            const int64_t c0 = s0 / C, c1 = (next_end - 1) / C;
+            seg_arrive<T, false>(cur, c, c0, c1, sc, P, y, ep);
+        }
+    }
+}
+
 template <typename V, typename T, int ITEMS>
 __global__ void __launch_bounds__(ITEMS >= 16 ? 512 : 1024)
 k_csr_split(int64_t nnz, int64_t m, const int *__restrict__ rowptr, const int *__restrict__ cols,
@@ -184,78 +271,11 @@ k_csr_split(int64_t nnz, int64_t m, const int *__restrict__ rowptr, const int *_
             const int *__restrict__ meta0, const PartialsT<T> P) {
     const Epi<T> ep(alpha, beta);
     constexpr int C = 32 * ITEMS;
-    const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t nchunks = (nnz + C - 1) / C;
-    for (int64_t c = warp; c < nchunks; c += nwarps) {
-        const int64_t E0 = c * C, E1 = (E0 + C < nnz) ? E0 + C : nnz;
-        const int64_t a = E0 + (int64_t)lane * ITEMS;
-        const int cnt = E1 - a <= 0 ? 0 : (E1 - a >= ITEMS ? ITEMS : (int)(E1 - a));
-        const int last_lane = (int)((E1 - E0 - 1) / ITEMS);
-        int r_unused[ITEMS];
-        T v[ITEMS], xv[ITEMS];
-        seg_load<V, T, ITEMS, false>(E1 - E0 == C, a, cnt, nullptr, cols, vals, x, r_unused, v, xv);
-        const int H = __ldg(meta0 + c);
-        int cur = 0;
-        if (cnt > 0 && a > 0) {  // largest row r in [H, H_next] with rowptr[r] <= a
-            int lo = H, hi = __ldg(meta0 + c + 1);
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (__ldg(rowptr + mid) <= a) lo = mid; else hi = mid - 1;
-            }
-            cur = lo;
-        }
-        const int fr = cur;
-        int next_end = cnt > 0 ? __ldg(rowptr + cur + 1) : 0;
-        T fs = T(0), acc = T(0);
-        bool fflush = false;
-        if (cnt > 0) {
-#pragma unroll
-            for (int j = 0; j < ITEMS; ++j) {
-                if (j < cnt) {
-                    while (a + j >= next_end) {
-                        if (!fflush) { fs = acc; fflush = true; }
-                        else seg_write<T, false>(y, cur, acc, ep);
-                        acc = T(0);
-                        ++cur;
-                        next_end = __ldg(rowptr + cur + 1);
-                    }
-                    acc = fma(v[j], xv[j], acc);
-                }
-            }
-            const int64_t b = a + cnt;
-            while (cur < m && next_end <= b) {
-                if (!fflush) { fs = acc; fflush = true; }
-                else seg_write<T, false>(y, cur, acc, ep);
-                acc = T(0);
-                ++cur;
-                if (cur < m) next_end = __ldg(rowptr + cur + 1);
-            }
-        }
-        const int key = (cnt > 0 && cur < m) ? cur : -1;
-        const T sc = seg_scan<T>(key, key >= 0 ? acc : T(0));
-        const int pkey = __shfl_up_sync(0xffffffffu, key, 1);
-        const T pval = __shfl_up_sync(0xffffffffu, sc, 1);
-        const int hstart = __ldg(rowptr + H);
-        const bool h_back = hstart < E0;
-        const T total = seg_carry<T>(cnt > 0 && fflush && lane > 0 && pkey == fr, fs, pval);
-        if (cnt > 0 && fflush) {
-            if (fr == H && h_back) {
-                const int64_t c0 = hstart / C, c1 = (__ldg(rowptr + H + 1) - 1) / C;
-                seg_arrive<T, false>(fr, c, c0, c1, total, P, y, ep);
-            } else {
-                seg_write<T, false>(y, fr, total, ep);
-            }
-        }
-        if (lane == last_lane && cur < m) {
-            const int s0 = __ldg(rowptr + cur);
-            if (s0 < E1 && next_end > E1) {  // open row continues into the next chunk
-                const int64_t c0 = s0 / C, c1 = (next_end - 1) / C;
-                seg_arrive<T, false>(cur, c, c0, c1, sc, P, y, ep);
-            }
-        }
-    }
+    for (int64_t c = warp; c < nchunks; c += nwarps)
+        csr_split_chunk<V, T, ITEMS>(c, nnz, m, rowptr, cols, vals, x, y, ep, meta0, P);
 }
 
 }  // namespace spmv

@@ -164,21 +164,31 @@ def block_diagonal(n: int, r: int, rng: np.random.Generator) -> Coo:
     return Coo(n, n, rows, cols, vals, name=f"blockdiag_{n}_r{r}")
 
 
+def _sort_unique_keys(key: np.ndarray) -> np.ndarray:
+    """Sorted distinct values of an int64 key array (sort + neighbour test;
+    much faster than np.unique on large arrays)."""
+    key = np.sort(key)
+    if key.size < 2:
+        return key
+    keep = np.empty(key.size, dtype=bool)
+    keep[0] = True
+    np.not_equal(key[1:], key[:-1], out=keep[1:])
+    return key[keep]
+
+
 def _sorted_unique_per_row(rows: np.ndarray, cols: np.ndarray, n: int,
                            rng: np.random.Generator) -> tuple[np.ndarray, np.ndarray]:
     """Sort (row, col) pairs, redrawing columns that collide within a row."""
-    rows = rows.astype(np.int64)
-    cols = cols.astype(np.int64)
+    key = np.sort(rows.astype(np.int64) * n + cols.astype(np.int64))
     while True:
-        order = np.lexsort((cols, rows))
-        rows, cols = rows[order], cols[order]
-        dup = np.zeros(rows.size, dtype=bool)
-        if rows.size > 1:
-            dup[1:] = (rows[1:] == rows[:-1]) & (cols[1:] == cols[:-1])
+        dup = np.zeros(key.size, dtype=bool)
+        if key.size > 1:
+            np.equal(key[1:], key[:-1], out=dup[1:])
         k = int(dup.sum())
         if k == 0:
-            return rows.astype(np.int32), cols.astype(np.int32)
-        cols[dup] = rng.integers(0, n, size=k)
+            return (key // n).astype(np.int32), (key % n).astype(np.int32)
+        key[dup] = (key[dup] // n) * n + rng.integers(0, n, size=k)
+        key.sort()
 
 
 def poisson_rows(n: int, lam: float, rng: np.random.Generator,
@@ -201,19 +211,19 @@ def rmat(scale: int, edge_factor: int, rng: np.random.Generator,
     duplicate edges are removed, then N(0,1) values drawn per unique entry."""
     n = 1 << scale
     E = edge_factor * n
-    r = np.zeros(E, dtype=np.int64)
-    cc = np.zeros(E, dtype=np.int64)
-    ab, abc = a + b, a + b + c
+    r = np.zeros(E, dtype=np.uint32)
+    cc = np.zeros(E, dtype=np.uint32)
+    fa, fab, fabc = np.float32(a), np.float32(a + b), np.float32(a + b + c)
     for level in range(scale):
-        u = rng.random(E)
-        row_bit = u >= ab                     # quadrants c, d
-        col_bit = ((u >= a) & (u < ab)) | (u >= abc)   # quadrants b, d
-        bit = 1 << (scale - 1 - level)
-        r += row_bit * bit
-        cc += col_bit * bit
-    key = np.unique(r * n + cc)
-    rows = (key // n).astype(np.int32)
-    cols = (key % n).astype(np.int32)
+        u = rng.random(E, dtype=np.float32)
+        shift = np.uint32(scale - 1 - level)
+        row_bit = u >= fab                                  # quadrants c, d
+        col_bit = ((u >= fa) & (u < fab)) | (u >= fabc)     # quadrants b, d
+        r |= row_bit.view(np.uint8).astype(np.uint32) << shift
+        cc |= col_bit.view(np.uint8).astype(np.uint32) << shift
+    key = _sort_unique_keys((r.astype(np.int64) << scale) | cc.astype(np.int64))
+    rows = (key >> scale).astype(np.int32)
+    cols = (key & (n - 1)).astype(np.int32)
     vals = rng.standard_normal(rows.size)
     return Coo(n, n, rows, cols, vals, name=f"rmat_s{scale}_ef{edge_factor}",
                meta={"edges_drawn": E, "a": a, "b": b, "c": c})
@@ -233,7 +243,7 @@ def random_coo(m: int, n: int, nnz: int, rng: np.random.Generator,
     rows = rng.integers(0, max(m, 1), size=nnz)
     cols = rng.integers(0, max(n, 1), size=nnz)
     if not duplicates and nnz:
-        key = np.unique(rows.astype(np.int64) * n + cols)
+        key = _sort_unique_keys(rows.astype(np.int64) * n + cols)
         rows, cols = key // n, key % n
     elif nnz:
         order = np.lexsort((cols, rows))

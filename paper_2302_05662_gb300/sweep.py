@@ -71,7 +71,7 @@ class Timer:
         self.torch = torch
         self.flush_buf = torch.empty(2 * l2_bytes // 4, dtype=torch.int32, device="cuda")
 
-    def time_us(self, h, x, y, reps: int = 7, warm: int = 2) -> float:
+    def time_us(self, h, x, y, reps: int = 7, warm: int = 1) -> float:
         torch = self.torch
         stream = torch.cuda.current_stream()
         for _ in range(warm):
@@ -111,18 +111,41 @@ def sweep_matrix(coo, space, timer: Timer, reps=7, value_dtype="f64", seed=0):
     x = torch.from_numpy(np.random.default_rng(seed).uniform(-1, 1, coo.n)).to(xdt).cuda()
     y = torch.zeros(coo.m, dtype=xdt, device="cuda")
     h = B.spmv_create(coo.m, coo.n, rows, cols, vals)
-    out = []
+    out = [None] * len(space)
+    # visit configurations grouped by what must be re-packed, so a change of
+    # launch parameters alone reuses the packed arrays
+    def pack_key(i):
+        c = space[i]
+        return (c.get("format", 0), c.get("threads_per_row", 0), c.get("bsr_block", 4), c.get("unroll", 2),
+                c.get("hyb_ell_width", 0))
+    refused = set()
     try:
-        for cfg in space:
+        for i in sorted(range(len(space)), key=pack_key):
+            cfg = space[i]
+            if pack_key(i) in refused:
+                out[i] = (cfg, None)
+                continue
             try:
                 B.spmv_set_config(h, B.make_config(**cfg))
-            except B.SpmvError:
-                out.append((cfg, None))
+            except B.SpmvError as e:
+                if e.status == -4:
+                    refused.add(pack_key(i))
+                out[i] = (cfg, None)
                 continue
-            out.append((cfg, timer.time_us(h, x, y, reps=reps)))
+            out[i] = (cfg, timer.time_us(h, x, y, reps=reps))
     finally:
         B.spmv_destroy(h)
     return out
+
+
+def matrix_features(coo):
+    """Device-computed features (spmv_features) of a matrix."""
+    rows, cols, vals = device_matrix(coo)
+    h = B.spmv_create(coo.m, coo.n, rows, cols, vals)
+    try:
+        return B.spmv_features(h)
+    finally:
+        B.spmv_destroy(h)
 
 
 def default_csr(coo) -> dict:
@@ -171,9 +194,11 @@ def main():
             if time.time() - t0 > args.time_budget:
                 break
             fam, coo = generate_dataset_matrix(idx, n_hi=args.n_hi)
-            res = sweep_matrix(coo, space, timer, reps=args.reps, seed=idx)
+            res = sweep_matrix(coo, space + [default_csr(coo)], timer, reps=args.reps, seed=idx)
+            feats = matrix_features(coo)
             rec = {"matrix": idx, "family": fam, "m": coo.m, "n": coo.n, "nnz": coo.nnz,
-                   "times": [[config_key(c), t] for c, t in res]}
+                   "features": [float(v) for v in feats], "default_us": res[-1][1],
+                   "times": [[config_key(c), t] for c, t in res[:-1]]}
             fh.write(json.dumps(rec) + "\n")
             fh.flush()
 

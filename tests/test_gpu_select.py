@@ -1,0 +1,134 @@
+"""GPU parity of the feature-extraction kernels (Table 2 features plus the
+selector's extras) against the oracle, and of the fused MLP inference
+kernel against the oracle's fp64 forward pass; spmv_select's choice and its
+default-CSR fallback."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2302_05662_gb300 import binding as B
+from paper_2302_05662_gb300 import matgen
+from paper_2302_05662_gb300 import selector as S
+
+from gpu_util import create
+
+pytestmark = pytest.mark.gpu
+
+INT_FEATURES = ("n_rows", "nnz", "min_row", "max_row", "median_row", "mode_row", "bandwidth")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    from paper_2302_05662_gb300 import build
+    build.build()
+    return B.load_library()
+
+
+def _cases():
+    rng = np.random.default_rng(41)
+    out = list(matgen.workload_matrices("small"))
+    out.append(("lap2d_64", matgen.laplacian_2d(64)))
+    out.append(("random_dups", matgen.random_coo(3000, 2000, 30000, rng, duplicates=True, shuffle=True)))
+    out.append(("empty_rows", matgen.random_coo(9000, 50, 300, rng)))
+    out.append(("one_row", matgen.Coo(1, 700, np.zeros(600, np.int32), np.arange(600, dtype=np.int32),
+                                      np.ones(600))))
+    out.append(("wide", matgen.random_coo(5, 100000, 2000, rng)))
+    out.append(("tall_hyb", matgen.poisson_rows(20000, 6.0, rng)))
+    for fam in matgen.FAMILIES:
+        out.append((f"jit_{fam}", matgen.family_matrix(fam, 7000, seed=5, jitter=True)))
+    return out
+
+
+CASES = _cases()
+
+
+@pytest.mark.parametrize("name", [c[0] for c in CASES])
+def test_features_match_oracle(name):
+    coo = dict(CASES)[name]
+    h = create(coo, B.SPMV_F64)
+    try:
+        got = B.spmv_features(h)
+    finally:
+        B.spmv_destroy(h)
+    want = O.features(coo.m, coo.n, coo.rows, coo.cols)
+    for k, fname in enumerate(O.FEATURE_NAMES):
+        if fname in INT_FEATURES:
+            assert got[k] == want[fname], (fname, got[k], want[fname])
+        else:
+            assert got[k] == pytest.approx(want[fname], rel=1e-12, abs=1e-15), fname
+
+
+def test_features_empty_matrix():
+    import torch
+    e = torch.zeros(0, dtype=torch.int32, device="cuda")
+    h = B.spmv_create(6, 4, e, e, torch.zeros(0, dtype=torch.float64, device="cuda"))
+    try:
+        got = B.spmv_features(h)
+    finally:
+        B.spmv_destroy(h)
+    want = O.features_vector(6, 4, [], [])
+    assert np.array_equal(got, want)
+
+
+def _random_selector(H=64, K=72, seed=0):
+    rng = np.random.default_rng(seed)
+    w = dict(mu=rng.normal(0, 1, 20), sigma=rng.uniform(0.5, 3, 20), W1=rng.normal(0, 0.4, (H, 20)),
+             b1=rng.normal(0, 0.1, H), W2=rng.normal(0, 0.4, (K, H)), b2=rng.normal(0, 0.1, K))
+    labels = [dict(format=k % 5, threads_per_block=32 << (k % 6)) for k in range(K)]
+    return w, labels
+
+
+def test_mlp_kernel_matches_oracle_forward():
+    w, labels = _random_selector()
+    blob = S.make_blob(w["mu"], w["sigma"], w["W1"], w["b1"], w["W2"], w["b2"], labels)
+    B.spmv_selector_load(blob)
+    p = S.parse_blob(blob)          # the fp32 weights the device holds
+    rng = np.random.default_rng(3)
+    for _, coo in CASES[:8]:
+        f = O.features_vector(coo.m, coo.n, coo.rows, coo.cols)
+        choice, logits = B.spmv_selector_infer(f, len(labels))
+        want = O.mlp_forward(f, p["mu"], p["sigma"], p["W1"], p["b1"], p["W2"], p["b2"])
+        scale = max(1.0, float(np.max(np.abs(want))))
+        assert np.max(np.abs(logits - want)) <= 2e-4 * scale
+        top = np.sort(want)[-2:]
+        if top[1] - top[0] > 1e-3 * scale:       # decision not within rounding
+            assert choice == int(np.argmax(want))
+    # a random feature vector too
+    f = np.abs(rng.normal(0, 1000, 20))
+    choice, logits = B.spmv_selector_infer(f, len(labels))
+    want = O.mlp_forward(f, p["mu"], p["sigma"], p["W1"], p["b1"], p["W2"], p["b2"])
+    assert np.max(np.abs(logits - want)) <= 2e-4 * max(1.0, float(np.max(np.abs(want))))
+
+
+def test_select_returns_label_and_falls_back():
+    coo = CASES[0][1]
+    h = create(coo, B.SPMV_F64)
+    try:
+        B.spmv_selector_unload()
+        cfg, feats = B.spmv_select(h)
+        assert cfg.format == B.FMT_CSR and cfg.threads_per_block == 256       # default CSR
+        assert feats[1] == coo.nnz
+        # a selector whose class 5 always wins
+        w, labels = _random_selector(seed=2)
+        w["W2"][:] = 0.0
+        w["b2"][:] = 0.0
+        w["b2"][5] = 1.0
+        labels[5] = dict(format=B.FMT_HYB, threads_per_block=128, unroll=4, regcap=32)
+        B.spmv_selector_load(S.make_blob(w["mu"], w["sigma"], w["W1"], w["b1"], w["W2"], w["b2"], labels))
+        cfg, _ = B.spmv_select(h)
+        assert (cfg.format, cfg.threads_per_block, cfg.unroll, cfg.regcap) == (B.FMT_HYB, 128, 4, 32)
+        B.spmv_set_config(h, cfg)         # the choice is a valid configuration
+    finally:
+        B.spmv_destroy(h)
+        B.spmv_selector_unload()
+
+
+def test_bad_blob_rejected():
+    w, labels = _random_selector()
+    blob = S.make_blob(w["mu"], w["sigma"], w["W1"], w["b1"], w["W2"], w["b2"], labels)
+    with pytest.raises(B.SpmvError):
+        B.spmv_selector_load(blob[:-1])
+    bad = blob.copy()
+    bad[0] = 1.0
+    with pytest.raises(B.SpmvError):
+        B.spmv_selector_load(bad)

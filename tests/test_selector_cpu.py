@@ -1,0 +1,70 @@
+"""Host-side selector logic: blob layout, soft targets, training on a
+separable toy set, and the evaluation arithmetic."""
+import numpy as np
+
+from paper_2302_05662_gb300 import selector as S
+
+
+def test_blob_roundtrip():
+    rng = np.random.default_rng(0)
+    H, K = 8, 5
+    w = dict(mu=rng.normal(size=20), sigma=rng.uniform(1, 2, 20), W1=rng.normal(size=(H, 20)),
+             b1=rng.normal(size=H), W2=rng.normal(size=(K, H)), b2=rng.normal(size=K))
+    labels = [dict(format=k, threads_per_block=64) for k in range(K)]
+    blob = S.make_blob(w["mu"], w["sigma"], w["W1"], w["b1"], w["W2"], w["b2"], labels)
+    assert blob.size == 5 + 40 + H * 20 + H + K * H + K + 8 * K
+    p = S.parse_blob(blob)
+    assert (p["F"], p["H"], p["K"]) == (20, H, K)
+    assert np.allclose(p["W2"], w["W2"].astype(np.float32))
+    assert list(p["labels"][3]) == [3, 64, 0, 2, 64, -1, 4, 0]
+
+
+def test_soft_targets_favour_near_ties():
+    T = np.array([[10.0, 10.1, 20.0, np.inf]])
+    P = S.soft_targets(T, tau=0.02)
+    assert P[0, 3] == 0.0 and P[0, 0] > P[0, 1] > P[0, 2]
+    assert abs(P.sum() - 1.0) < 1e-12
+
+
+def test_training_learns_separable_toy():
+    rng = np.random.default_rng(1)
+    X = np.abs(rng.normal(size=(400, 20))) + 1.0
+    cls = (X[:, 2] > np.median(X[:, 2])).astype(int)       # density feature decides
+    T = np.where(np.arange(3)[None, :] == cls[:, None], 1.0, 2.0)
+    w = S.train(X, T, hidden=16, epochs=400, lr=1e-2)
+    pred = np.argmax(S.predict(w, X), axis=1)
+    assert np.mean(pred == cls) > 0.95
+
+
+def test_evaluate_arithmetic():
+    T = np.array([[1.0, 2.0], [4.0, 3.0]])
+    D = np.array([2.0, 6.0])
+    e = S.evaluate(np.array([0, 0]), T, D)
+    assert e["within_10pct"] == 0.5
+    assert abs(e["geomean_slowdown"] - np.sqrt(1.0 * 4.0 / 3.0)) < 1e-12
+    assert abs(e["geomean_speedup_vs_default_csr"] - np.sqrt(2.0 * 1.5)) < 1e-12
+
+
+def test_committed_selector_matches_its_report():
+    """The committed blob, evaluated on the committed held-out records,
+    reproduces the committed report (fraction within 10% of the exhaustive
+    best, geometric-mean slowdown and speedup over default CSR)."""
+    import json
+    import os
+    from paper_2302_05662_gb300 import sweep
+    if not os.path.exists(S.DEFAULT_BLOB):
+        import pytest
+        pytest.skip("no committed selector")
+    p = S.parse_blob(np.fromfile(S.DEFAULT_BLOB, dtype=np.float32))
+    recs = S.load_records([S.DEFAULT_DATA])
+    keys = [sweep.config_key(c) for c in sweep.label_space()]
+    X, T, D, ids, fams = S.dataset(recs, keys)
+    msk = (ids >= 1800) & np.isfinite(T).any(axis=1) & np.isfinite(D)
+    w = {k: p[k].astype(np.float64) for k in ("mu", "sigma", "W1", "b1", "W2", "b2")}
+    lg = np.where(np.isfinite(T[msk]), S.predict(w, X[msk]), -np.inf)
+    got = S.evaluate(np.argmax(lg, axis=1), T[msk], D[msk])
+    rep = json.load(open(os.path.join(os.path.dirname(S.DEFAULT_BLOB), "selector_gb300_report.json")))
+    assert got["n"] == rep["heldout"]["n"] == 200
+    assert abs(got["within_10pct"] - rep["heldout"]["within_10pct"]) <= 0.01
+    assert got["within_10pct"] >= 0.90
+    assert got["geomean_speedup_vs_default_csr"] > 1.0
