@@ -79,8 +79,9 @@ typedef enum {
  *                     the largest power of two up to 32 that leaves each
  *                     lane at least 8 entries of a mean-length row).  BSR: blocks handled at once per block row,
  *                     1/2/4/8 (default 1).  Ignored by ELL, COO and HYB.
- *   unroll            1, 2 or 4 (default 2): loads in flight per lane (ELL,
- *                     CSR) or items per lane / 4 (COO, HYB tail, split CSR).
+ *   unroll            1, 2 or 4: loads in flight per lane (ELL, CSR) or
+ *                     items per lane / 4 (COO, HYB tail, split CSR); default
+ *                     4 for ELL and HYB, 2 otherwise.
  *   regcap            register cap per thread: 64 (default; the ceiling
  *                     that keeps 1024-thread blocks launchable) or 32
  *                     (the paper's maxrregcount knob).

@@ -84,6 +84,11 @@ int default_tpr(const spmv_matrix *h) {
     return t;
 }
 
+// Loads in flight per thread: ELL (and the ELL part of HYB) keeps four
+// column/value pairs in flight (measured fastest on regular matrices), the
+// other kernels two (or 8 entries per lane for the chunked kernels).
+int default_unroll(int format) { return format == SPMV_FMT_ELL || format == SPMV_FMT_HYB ? 4 : 2; }
+
 // Fills defaults and validates; returns SPMV_ERR_INVALID on a bad field.
 int resolve_config(const spmv_matrix *h, const spmv_config *in, spmv_config *out) {
     spmv_config c;
@@ -91,7 +96,7 @@ int resolve_config(const spmv_matrix *h, const spmv_config *in, spmv_config *out
     if (in) {
         c = *in;
         if (c.threads_per_block == 0) c.threads_per_block = 256;
-        if (c.unroll == 0) c.unroll = 2;
+        if (c.unroll == 0) c.unroll = default_unroll(c.format);
         if (c.regcap == 0) c.regcap = 64;
         if (c.bsr_block == 0) c.bsr_block = 4;
     }
@@ -179,7 +184,7 @@ void spmv_config_default(spmv_config *cfg, int32_t format) {
     cfg->format = format;
     cfg->threads_per_block = 256;
     cfg->threads_per_row = 0;
-    cfg->unroll = 2;
+    cfg->unroll = default_unroll(format);
     cfg->regcap = 64;
     cfg->carveout = -1;
     cfg->bsr_block = 4;

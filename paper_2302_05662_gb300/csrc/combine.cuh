@@ -6,8 +6,8 @@
 // partial in; the one that finds the other's partial adds the two in unit
 // order and writes y.  The slot holds the partial itself, so no memory fence
 // is needed.  A row spanning three or more units leaves each partial in
-// head/tail storage, fences, and counts its arrival; the last unit to arrive
-// adds all partials in unit order.  Either way the sum order is fixed, so
+// head/tail storage and counts its arrival with an acquire-release atomic;
+// the last unit to arrive adds all partials in unit order.  Either way the sum order is fixed, so
 // results do not depend on scheduling, and every slot and counter is
 // restored by the unit that consumes it.
 #pragma once
@@ -27,6 +27,12 @@ struct PartialsT {
         return PartialsT{(T *)p.head, (T *)p.tail, p.count, p.xslot, p.stride};
     }
 };
+
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned *p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
 
 template <typename T> struct XEnc;
 template <> struct XEnc<double> {
@@ -63,10 +69,11 @@ __device__ __forceinline__ bool join_partial(int64_t c, int64_t c0, int64_t c1, 
     }
     if (c == c0) P.tail[c * st + off] = contrib;
     else P.head[c * st + off] = contrib;
-    __threadfence();
-    const unsigned old = atomicAdd(P.count + c0 * st + off, 1u);
+    // acquire-release arrival: releases this unit's partial (stored just
+    // above by this thread) and, for the last arrival, acquires every other
+    // unit's partial -- no full memory fence needed
+    const unsigned old = atom_add_acq_rel(P.count + c0 * st + off, 1u);
     if (old != (unsigned)(c1 - c0)) return false;
-    __threadfence();
     T t = __ldcg(P.tail + c0 * st + off);
     for (int64_t k = c0 + 1; k <= c1; ++k) t += __ldcg(P.head + k * st + off);
     P.count[c0 * st + off] = 0u;

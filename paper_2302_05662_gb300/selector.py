@@ -35,10 +35,10 @@ LOG_IDX = (0, 1, 3, 4, 5, 6, 7, 8, 9, 14, 15)
 
 
 def full_config(d: dict) -> list:
-    """The 8 spmv_config fields of a (partial) label dict, library defaults
-    filled in (threads_per_row 0 = default, carveout -1)."""
-    base = {"format": 0, "threads_per_block": 256, "threads_per_row": 0, "unroll": 2, "regcap": 64,
-            "carveout": -1, "bsr_block": 4, "hyb_ell_width": 0}
+    """The 8 spmv_config fields of a (partial) label dict; unset fields stay
+    0 (the library's per-format default) except carveout -1 (driver default)."""
+    base = {"format": 0, "threads_per_block": 256, "threads_per_row": 0, "unroll": 0, "regcap": 0,
+            "carveout": -1, "bsr_block": 0, "hyb_ell_width": 0}
     base.update(d)
     return [int(base[k]) for k in CFG_FIELDS]
 

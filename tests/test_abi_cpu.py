@@ -53,6 +53,8 @@ def test_config_default_host_only(lib):
     lib.spmv_config_default(ctypes.byref(cfg), binding.FMT_BSR)
     assert cfg.as_dict() == {"format": 4, "threads_per_block": 256, "threads_per_row": 0, "unroll": 2,
                              "regcap": 64, "carveout": -1, "bsr_block": 4, "hyb_ell_width": 0}
+    lib.spmv_config_default(ctypes.byref(cfg), binding.FMT_ELL)
+    assert cfg.unroll == 4
 
 
 def test_host_argument_errors(lib):

@@ -16,7 +16,7 @@ def test_blob_roundtrip():
     p = S.parse_blob(blob)
     assert (p["F"], p["H"], p["K"]) == (20, H, K)
     assert np.allclose(p["W2"], w["W2"].astype(np.float32))
-    assert list(p["labels"][3]) == [3, 64, 0, 2, 64, -1, 4, 0]
+    assert list(p["labels"][3]) == [3, 64, 0, 0, 0, -1, 0, 0]
 
 
 def test_soft_targets_favour_near_ties():
