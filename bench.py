@@ -217,6 +217,15 @@ def cpu_baseline(mats_host):
 
 
 NAMES = ("stencil27_128^3", "poisson16_2^20", "rmat_s20_ef16", "banded_2^20_w32", "blockdiag4_2^20")
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+# one ncu --set full capture of the kernel as it is now, per (kernel, matrix,
+# value type); summaries and commands in profiles/.  A kernel missing here
+# reports traffic null.
+NCU_TRAFFIC = {
+    ("bsr", "banded_2^20_w32", "f64"): (602.3e6, "profiles/bsr_banded_2p20_w32_f64.md"),
+    ("ell", "stencil27_128^3", "f64"): (693.8e6, "profiles/ell_stencil27_128_f64.md"),
+}
 FMT_KEYS = {0: "csr", 1: "ell", 2: "coo", 3: "hyb", 4: "bsr"}
 
 
@@ -346,9 +355,15 @@ def ours(args, world, rank, local):
         rows, cols, vals = sweep.device_matrix(coo, args.dtype)
         x = torch.from_numpy(x_np).to(xdt).cuda()
         y = torch.zeros(coo.m, dtype=xdt, device="cuda")
-        h = B.spmv_create(coo.m, coo.n, rows, cols, vals)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = B.spmv_create(coo.m, coo.n, rows, cols, vals)     # COO -> CSR on the device
+        t_create = time.perf_counter() - t0
         del rows, cols, vals
         nnz = B.spmv_get_info(h).nnz
+        t0 = time.perf_counter()
+        B.spmv_features(h)
+        t_feat = time.perf_counter() - t0
         nbytes = byte_model(coo.m, coo.n, nnz, vsz, xsz)
         if args.fixed:
             from paper_2302_05662_gb300.workload import SWEEP_VARIANTS
@@ -363,15 +378,25 @@ def ours(args, world, rank, local):
             format_sweep.append({"matrix": mname, "kernel": fname, "config": cfg, "us": round(t, 2),
                                  "gflops": round(2 * nnz / (t * 1e-6) / 1e9, 1), "gbs": round(gbs, 1)})
         chosen, source = best_cfg, ("fixed" if args.fixed else "exhaustive")
+        t_sel = t_pack = None
         if have_selector and not args.fixed:
+            B.spmv_set_config(h, B.make_config(format=B.FMT_CSR))
+            t0 = time.perf_counter()
             sel_cfg, _ = B.spmv_select(h)
+            t_select = time.perf_counter() - t0
+            t0 = time.perf_counter()
             B.spmv_set_config(h, sel_cfg)
+            t_pack = time.perf_counter() - t0
             t_sel = timer.time_us(h, x, y, reps=5)
             chosen = {kk: getattr(sel_cfg, kk) for kk, _ in sel_cfg._fields_}
             source = "selector"
             selector_rows.append({"matrix": mname, "selected": fmt_name(chosen), "selected_us": round(t_sel, 2),
                                   "best": fmt_name(best_cfg), "best_us": round(best_t, 2),
-                                  "slowdown": round(t_sel / best_t, 4)})
+                                  "slowdown": round(t_sel / best_t, 4),
+                                  "overhead_ms": {"coo_to_csr": round(t_create * 1e3, 2),
+                                                  "features": round(t_feat * 1e3, 3),
+                                                  "select": round(t_select * 1e3, 3),
+                                                  "pack_selected": round(t_pack * 1e3, 2)}})
         else:
             B.spmv_set_config(h, B.make_config(**best_cfg))
         info = B.spmv_get_info(h)
@@ -457,8 +482,10 @@ def ours(args, world, rank, local):
     dom = max(range(len(mats)), key=lambda i: per_ms[i])
     dp = mats[dom]
     achieved = dp["bytes"] / (per_ms[dom] * 1e-3) / 1e9
+    tr = NCU_TRAFFIC.get((fmt_name(dp["cfg"]), dp["matrix"], args.dtype))
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
+                "frac": round(achieved / peak, 4), "traffic": tr[0] if tr else None,
+                "traffic_source": tr[1] if tr else None,
                 "kernel": f"{fmt_name(dp['cfg'])} on {dp['matrix']}",
                 "algorithmic_bytes_per_launch": dp["bytes"], "peak_source": peak_kind,
                 "time_share": round(per_ms[dom] / sum(per_ms), 3)}

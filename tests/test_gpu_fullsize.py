@@ -1,13 +1,21 @@
 """Parity at the benchmark's full sizes and launch configurations: the five
 format-sweep matrices (27-point stencil 128^3, Poisson(16) rows 2^20, R-MAT
 scale 20, banded 2^20 half-width 32, block-diagonal 4x4 2^20), every kernel
-variant the benchmark times, in fp64, fp32 and bf16, against the fp64 oracle
-over all rows (the oracle is a single pass over the triplets)."""
+variant of the sweep at its default configuration plus the configuration
+the selector picks (the one bench.py times), in fp64, fp32 and bf16, against
+the fp64 oracle over all rows (the oracle is one pass over the triplets).
+
+With SPMV_ERROR_REPORT=<path> the normwise error of every result is
+appended to that file as JSON lines."""
+import json
+import os
+
 import numpy as np
 import pytest
 
 from paper_2302_05662_gb300 import binding as B
 from paper_2302_05662_gb300 import matgen
+from paper_2302_05662_gb300 import selector as S
 from paper_2302_05662_gb300.workload import SWEEP_VARIANTS
 
 from gpu_util import TOL, VT_NAMES, create, oracle_for, rel_err, run
@@ -29,21 +37,41 @@ def test_full_size_sweep(oracle, mname):
     coo = next(c for n, c in matgen.workload_matrices("full", only=mname))
     k = NAMES.index(mname)
     x = matgen.dense_vector(coo.n, 100 + k)       # the benchmark's x for this matrix
-    failures = []
+    report = os.environ.get("SPMV_ERROR_REPORT")
+    have_sel = os.path.exists(S.DEFAULT_BLOB)
+    if have_sel:
+        S.load_default_selector()
+    failures, records = [], []
     for vt in (B.SPMV_F64, B.SPMV_F32, B.SPMV_BF16):
         want = oracle_for(oracle, coo, vt, x)
-        for vname, kw in SWEEP_VARIANTS:
+        want64 = oracle.spmv_coo_obj(coo, x) if vt != B.SPMV_F64 else want
+        variants = [(n, B.make_config(**kw)) for n, kw in SWEEP_VARIANTS]
+        if have_sel:
+            h = create(coo, vt)
             try:
-                h = create(coo, vt, B.make_config(**kw))
+                sel, _ = B.spmv_select(h)
+            finally:
+                B.spmv_destroy(h)
+            variants.append(("selected", sel))
+        for vname, cfg in variants:
+            try:
+                h = create(coo, vt, cfg)
             except B.SpmvError as e:
                 # ELL / BSR padded storage over the limit (R-MAT; BSR also Poisson rows)
-                assert vname in ("ell", "bsr") and e.status == -4, str(e)
+                assert cfg.format in (B.FMT_ELL, B.FMT_BSR) and e.status == -4, str(e)
                 continue
             try:
                 got = run(h, vt, x, m=coo.m)
             finally:
                 B.spmv_destroy(h)
             err = rel_err(got, want)
+            records.append({"matrix": mname, "kernel": vname, "format": int(cfg.format),
+                            "dtype": VT_NAMES[vt], "err_vs_oracle_on_device_inputs": err,
+                            "err_vs_fp64_oracle_original_inputs": rel_err(got, want64)})
             if not err <= TOL[vt]:
                 failures.append(f"{vname}/{VT_NAMES[vt]}: {err:.3e}")
+    if report:
+        with open(report, "a") as fh:
+            for r in records:
+                fh.write(json.dumps(r) + "\n")
     assert not failures, failures
