@@ -15,6 +15,10 @@ Contents (each function cites the part of the paper it follows):
 * ``hyb_ell_width`` -- the ELL width rule used for the HYB format.
 * ``mlp_forward``   -- the selector's 2-layer MLP (Section 5.4 relies on
                        multi-class classification; this is its forward pass).
+* ``cg``            -- conjugate gradients (Hestenes-Stiefel) with its
+                       products from ``spmv_coo``: the iterative solver whose
+                       repeated SpMV amortises selection and conversion
+                       (Section 7.5).
 
 Parity pins: every function here is checked in ``tests/test_oracle_*.py``
 against closed forms, invariants, brute force or values printed in the paper.
@@ -275,3 +279,70 @@ def mlp_forward(fvec, mu, sigma, W1, b1, W2, b2) -> np.ndarray:
     z = mlp_inputs(fvec, mu, sigma)
     h = np.maximum(np.asarray(W1, np.float64) @ z + np.asarray(b1, np.float64), 0.0)
     return np.asarray(W2, np.float64) @ h + np.asarray(b2, np.float64)
+
+
+# ---------------------------------------------------------------------------
+# Conjugate gradients: the repeated-SpMV setting of Section 7.5
+# ---------------------------------------------------------------------------
+
+def _dot(a: np.ndarray, b: np.ndarray) -> float:
+    """Dot product: the fp64 products summed exactly (one final rounding)."""
+    import math
+    return math.fsum((np.asarray(a, np.float64) * np.asarray(b, np.float64)).tolist())
+
+
+def cg(m: int, rows, cols, vals, b, x0=None, tol: float = 1e-8,
+       maxit: int = 1000, record: bool = False) -> dict:
+    """Conjugate gradients (Hestenes and Stiefel, 1952) for A x = b with A
+    symmetric positive definite, given by COO triplets.
+
+    Section 7.5 names the preconditioned conjugate gradient method as the
+    iterative setting in which one matrix is multiplied many times, so the
+    selection and conversion cost is paid once.  The method itself is the
+    textbook one:
+
+        r_0 = b - A x_0,  p_0 = r_0,  rho_0 = r_0.r_0
+        while k < maxit and rho_k > tol^2 * (b.b):
+            q = A p_k;  pq = p_k.q          (stop: breakdown if pq <= 0)
+            alpha = rho_k / pq
+            x_{k+1} = x_k + alpha p_k;  r_{k+1} = r_k - alpha q
+            rho_{k+1} = r_{k+1}.r_{k+1};  beta = rho_{k+1} / rho_k
+            p_{k+1} = r_{k+1} + beta p_k
+
+    Products by ``spmv_coo``; dot products rounded once (``_dot``); each
+    vector update is one multiply and one add per element, each rounded.
+    Returns x, iterations (products A p), rho history (rho_0 .. rho_iters),
+    converged, breakdown; with ``record`` also the lists of r_k and p_k.
+    """
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(m) if x0 is None else np.array(x0, dtype=np.float64)
+    r = spmv_coo(m, m, rows, cols, vals, x, -1.0, 1.0, b)
+    p = r.copy()
+    rho = _dot(r, r)
+    stop = tol * tol * _dot(b, b)
+    hist = [rho]
+    rs, ps = ([r.copy()], [p.copy()]) if record else (None, None)
+    k = 0
+    breakdown = False
+    while k < maxit and rho > stop:
+        q = spmv_coo(m, m, rows, cols, vals, p)
+        pq = _dot(p, q)
+        if not pq > 0.0:
+            breakdown = True
+            break
+        alpha = rho / pq
+        x = x + alpha * p
+        r = r - alpha * q
+        rho_new = _dot(r, r)
+        p = r + (rho_new / rho) * p
+        rho = rho_new
+        hist.append(rho)
+        k += 1
+        if record:
+            rs.append(r.copy())
+            ps.append(p.copy())
+    out = {"x": x, "iterations": k, "rho": hist, "converged": rho <= stop,
+           "breakdown": breakdown}
+    if record:
+        out["r"], out["p"] = rs, ps
+    return out
