@@ -226,7 +226,7 @@ NCU_TRAFFIC = {
     ("bsr", "banded_2^20_w32", "f64"): (602.3e6, "profiles/bsr_banded_2p20_w32_f64.md"),
     ("ell", "stencil27_128^3", "f64"): (693.8e6, "profiles/ell_stencil27_128_f64.md"),
 }
-FMT_KEYS = {0: "csr", 1: "ell", 2: "coo", 3: "hyb", 4: "bsr"}
+FMT_KEYS = {0: "csr", 1: "ell", 2: "coo", 3: "hyb", 4: "bsr", 5: "sell"}
 
 
 def fmt_name(cfg: dict) -> str:
@@ -234,11 +234,18 @@ def fmt_name(cfg: dict) -> str:
     return "csr_split" if n == "csr" and cfg.get("threads_per_row") == -1 else n
 
 
+def format_bytes_of(B, h, cfg, m, n, xsz):
+    """Bytes the configured kernel itself reads (its format arrays) plus x
+    and y once: the format-actual counterpart of the byte model."""
+    B.spmv_set_config(h, B.make_config(**cfg))
+    return B.spmv_get_info(h).format_bytes + xsz * (n + m)
+
+
 def tune_matrix(B, sweep, h, coo, x, y, timer, reps):
     """Exhaustive search on one handle: the label space, then register cap x
     unroll x carveout around the winner.  Returns (best cfg, best us,
     per-format best {name: (cfg, us)})."""
-    space = sweep.label_space()
+    space = sweep.label_space(include_sell=True)
     times = []
     for cfg in space:
         try:
@@ -375,8 +382,10 @@ def ours(args, world, rank, local):
             best_cfg, best_t, per_fmt = tune_matrix(B, sweep, h, coo, x, y, timer, reps=5)
         for fname, (cfg, t) in sorted(per_fmt.items()):
             gbs = nbytes / (t * 1e-6) / 1e9
+            fb = format_bytes_of(B, h, cfg, coo.m, coo.n, xsz)
             format_sweep.append({"matrix": mname, "kernel": fname, "config": cfg, "us": round(t, 2),
-                                 "gflops": round(2 * nnz / (t * 1e-6) / 1e9, 1), "gbs": round(gbs, 1)})
+                                 "gflops": round(2 * nnz / (t * 1e-6) / 1e9, 1), "gbs": round(gbs, 1),
+                                 "format_gbs": round(fb / (t * 1e-6) / 1e9, 1)})
         chosen, source = best_cfg, ("fixed" if args.fixed else "exhaustive")
         t_sel = t_pack = None
         if have_selector and not args.fixed:
@@ -491,6 +500,7 @@ def ours(args, world, rank, local):
                 "time_share": round(per_ms[dom] / sum(per_ms), 3)}
     for fs in format_sweep:
         fs["frac"] = round(fs["gbs"] / peak, 4)
+        fs["format_frac"] = round(fs["format_gbs"] / peak, 4)
     clocks = clk.summary()
     batched = None
     if not args.no_batched and only is None and not args.fixed:

@@ -63,7 +63,9 @@ typedef enum {
     SPMV_FMT_ELL = 1, /* Section 2.3: m x max_nnz padded, column-major     */
     SPMV_FMT_COO = 2, /* (row, col, val) triplets sorted by row            */
     SPMV_FMT_HYB = 3, /* ELL part + COO overflow                           */
-    SPMV_FMT_BSR = 4  /* r x r dense blocks (blocked format of Sec. 2.3)   */
+    SPMV_FMT_BSR = 4, /* r x r dense blocks (blocked format of Sec. 2.3)   */
+    SPMV_FMT_SELL = 5 /* sliced ELL, 32-row slices of rows sorted by      */
+                      /* descending length (Sec. 2.3 SELL)                 */
 } spmv_format;
 
 /* threads_per_row value that selects the nnz-balanced CSR kernel. */
@@ -78,10 +80,12 @@ typedef enum {
  *                     SPMV_TPR_SPLIT for the nnz-balanced split (default:
  *                     the largest power of two up to 32 that leaves each
  *                     lane at least 8 entries of a mean-length row).  BSR: blocks handled at once per block row,
- *                     1/2/4/8 (default 1).  Ignored by ELL, COO and HYB.
- *   unroll            1, 2 or 4: loads in flight per lane (ELL, CSR) or
- *                     items per lane / 4 (COO, HYB tail, split CSR); default
- *                     4 for ELL and HYB, 2 otherwise.
+ *                     1/2/4/8 (default 1).  Ignored by ELL, COO, HYB and
+ *                     SELL (one lane per row).
+ *   unroll            1, 2 or 4 (8 also for ELL, HYB and SELL): loads in
+ *                     flight per lane (ELL, SELL, CSR) or items per lane / 4
+ *                     (COO, HYB tail, split CSR; at most 16 items); default
+ *                     4 for ELL, HYB and SELL, 2 otherwise.
  *   regcap            register cap per thread: 64 (default; the ceiling
  *                     that keeps 1024-thread blocks launchable) or 32
  *                     (the paper's maxrregcount knob).
@@ -113,6 +117,7 @@ typedef struct {
     int64_t ell_width;    /* ELL width (ELL), or ELL-part width (HYB)      */
     int64_t hyb_coo_nnz;  /* entries in the HYB COO part                   */
     int64_t bsr_blocks;   /* nonzero r x r blocks (BSR)                    */
+    int64_t sell_slots;   /* stored entries incl. padding (SELL)           */
     int64_t format_bytes; /* device bytes the active format's kernel reads */
     int32_t value_type;   /* spmv_dtype                                    */
     int32_t format;       /* active spmv_format                            */
@@ -135,7 +140,7 @@ SPMV_API void spmv_config_default(spmv_config *cfg, int32_t format);
  * or any triplet outside [0,m) x [0,n) (checked on the device);
  * SPMV_ERR_UNSUPPORTED for m, n or nnz >= 2^31 or a format whose padded
  * storage exceeds 8 nnz + 2^24 value slots (ELL width x rows; BSR blocks x
- * r^2); SPMV_ERR_OOM; SPMV_ERR_CUDA.
+ * r^2; SELL slices x 32 x slice width); SPMV_ERR_OOM; SPMV_ERR_CUDA.
  * Synchronises `stream`.
  */
 SPMV_API int spmv_create(spmv_handle *out, int64_t m, int64_t n, int64_t nnz,
@@ -183,7 +188,13 @@ typedef enum {
     SPMV_ARR_BSR_ROWPTR = 8,  /* int32[ceil(m/r)+1]                          */
     SPMV_ARR_BSR_COLIDX = 9,  /* int32[blocks]: block column                 */
     SPMV_ARR_BSR_VALS = 10,   /* value_type[blocks][r][r], row-major blocks  */
-    SPMV_ARR_ELL_PITCH = 11   /* (size query only) pitch in elements          */
+    SPMV_ARR_ELL_PITCH = 11,  /* (size query only) pitch in elements          */
+    SPMV_ARR_SELL_PTR = 12,   /* int32[slices+1]: first slot of each slice     */
+    SPMV_ARR_SELL_COLIDX = 13,/* int32[slots]: slice s, entry k, lane l at     */
+                              /* ptr[s] + 32 k + l; -1 = padding               */
+    SPMV_ARR_SELL_VALS = 14,  /* value_type[slots], 0 = padding                */
+    SPMV_ARR_SELL_PERM = 15   /* int32[m]: matrix row held by sorted row p     */
+                              /* (rows sorted by descending length, stable)    */
 } spmv_array_id;
 
 /*
@@ -268,10 +279,15 @@ SPMV_API int spmv_features(spmv_handle h, double *h_out, void *stream);
 /*
  * Load the selector: a 2-layer MLP classifier (Section 5.4: one classifier
  * mapping features to the best configuration) for the current device.
- * h_blob holds `count` floats: magic 2302, version 1, F (= 20), H, K; then
- * mu[F], sigma[F] (input standardisation after log1p of the count-like
- * features 0,1,3-9,14,15), W1[H][F], b1[H], W2[K][H], b2[K]; then K label
- * configurations of 8 values each (the spmv_config fields in order).
+ * h_blob holds `count` floats: magic 2302, version (1 or 2), F (= 20), H,
+ * K; then mu[F], sigma[F] (input standardisation after log1p of the
+ * count-like features 0,1,3-9,14,15), W1[H][F], b1[H], W2[K][H], b2[K];
+ * then K label configurations of 8 values each (the spmv_config fields in
+ * order; 0 = library default).  Version 2 appends the time head W3[K+1][H],
+ * b3[K+1] (natural log of microseconds per product for each label class,
+ * then for default CSR, linear in the hidden layer) and the conversion-cost
+ * model: for each format 0..5, {a, b, c} with cost a + b nnz + c m in
+ * microseconds.
  * H <= 256, K <= 512.  Copies the weights to the device.  A NULL blob with
  * count 0 unloads the selector.  Errors: SPMV_ERR_INVALID for a malformed
  * blob.
@@ -338,6 +354,78 @@ SPMV_API int spmv_batch_destroy(spmv_batch_handle b);
 SPMV_API int spmv_batch_run(const spmv_handle *hs, int32_t count,
                             const double *alpha, const void *const *d_x,
                             const double *beta, void *const *d_y, void *stream);
+
+/*
+ * Run-time mode decision (Section 5.3 steps 3-4: estimate the optimisation
+ * overhead, convert only if the predicted benefit is larger).
+ */
+typedef struct {
+    int32_t convert;               /* 1: converting pays off over expected_runs */
+    int32_t current_class;         /* label class of the handle's configuration,
+                                      -1 when it is default CSR (own time head) */
+    int32_t selected_class;        /* label class the classifier picks          */
+    int32_t pad;
+    double predicted_us_current;   /* predicted time of one product, now        */
+    double predicted_us_selected;  /* ... in the selected configuration         */
+    double predicted_pack_us;      /* predicted conversion (re-pack) time       */
+    double measured_select_us;     /* features + inference, measured            */
+} spmv_runtime_decision;
+
+/*
+ * Like spmv_select, plus the decision: with a version-2 selector (time head
+ * predicting the log-time of every label configuration and of default CSR,
+ * and a per-format conversion-cost model a + b nnz + c m), *out->convert is
+ * 1 when (predicted current time - predicted selected time) x expected_runs
+ * exceeds the measured feature + inference time plus the predicted
+ * conversion time.  The handle is not changed; apply *out_cfg with
+ * spmv_set_config when convert is 1.  Errors: SPMV_ERR_INVALID without a
+ * version-2 selector.  Synchronises `stream`.
+ */
+SPMV_API int spmv_select_runtime(spmv_handle h, int64_t expected_runs,
+                                 spmv_config *out_cfg, spmv_runtime_decision *out,
+                                 void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Conjugate gradients with the handle's SpMV.  Section 7.5 names the
+ * (preconditioned) conjugate gradient method as the iterative setting in
+ * which one matrix is multiplied many times, so feature extraction,
+ * selection and conversion are paid once.  The iteration is Hestenes and
+ * Stiefel's, unpreconditioned:
+ *   r_0 = b - A x_0, p_0 = r_0, rho_k = r_k.r_k;
+ *   while k < maxit and rho_k > tol^2 (b.b):
+ *     q = A p_k; stop with breakdown = 1 if p_k.q <= 0;
+ *     alpha = rho_k / (p_k.q); x += alpha p_k; r -= alpha q;
+ *     p_{k+1} = r_{k+1} + (rho_{k+1} / rho_k) p_k.
+ * A must be square and symmetric positive definite; every product runs in
+ * the handle's current format and configuration.
+ *
+ * d_b: device, m entries (double for SPMV_F64 handles, float otherwise),
+ *      read only.  d_x: device, same type; in: x_0, out: the last iterate.
+ * d_rho: NULL, or device double[maxit + 1] receiving rho_0 .. rho_iterations.
+ * Dot products accumulate in fp64 in a fixed order (repeat calls are
+ * bit-identical).  The whole loop is one CUDA graph whose WHILE node the
+ * device stops: no host round trip per iteration.  The handle keeps the
+ * graph and three m-vectors of scratch for the next call with the same
+ * (d_b, d_x, tol, maxit); spmv_set_config and spmv_destroy release them.
+ * Synchronises `stream`, then fills *out.
+ * Errors: SPMV_ERR_INVALID (NULL handle/result/vector, m != n, tol < 0 or
+ * not finite, maxit < 0 or > SPMV_CG_MAX_ITERATIONS), SPMV_ERR_CUDA.
+ * ------------------------------------------------------------------------- */
+#define SPMV_CG_MAX_ITERATIONS 16777216
+
+typedef struct {
+    int32_t iterations;  /* products A p_k performed */
+    int32_t converged;   /* rho_iterations <= tol^2 (b.b) */
+    int32_t breakdown;   /* stopped on p_k.A p_k <= 0 (A not SPD) */
+    int32_t reserved;
+    double rho0;         /* r_0.r_0 */
+    double rho;          /* r.r at exit (the recursively updated residual) */
+    double bb;           /* b.b */
+} spmv_cg_result;
+
+SPMV_API int spmv_cg(spmv_handle h, const void *d_b, void *d_x, double tol,
+                     int32_t maxit, double *d_rho, spmv_cg_result *out,
+                     void *stream);
 
 /* Frees every device array of the handle.  NULL is accepted. */
 SPMV_API int spmv_destroy(spmv_handle h);

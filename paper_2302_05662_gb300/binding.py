@@ -18,18 +18,20 @@ SPMV_OK = 0
 STATUS_NAMES = {0: "SPMV_OK", -1: "SPMV_ERR_INVALID", -2: "SPMV_ERR_OOM", -3: "SPMV_ERR_CUDA",
                 -4: "SPMV_ERR_UNSUPPORTED", -5: "SPMV_ERR_BOUNDS", -6: "SPMV_ERR_TIMEOUT"}
 SPMV_F64, SPMV_F32, SPMV_BF16 = 0, 1, 2
-FMT_CSR, FMT_ELL, FMT_COO, FMT_HYB, FMT_BSR = 0, 1, 2, 3, 4
-FORMAT_NAMES = {FMT_CSR: "csr", FMT_ELL: "ell", FMT_COO: "coo", FMT_HYB: "hyb", FMT_BSR: "bsr"}
+FMT_CSR, FMT_ELL, FMT_COO, FMT_HYB, FMT_BSR, FMT_SELL = 0, 1, 2, 3, 4, 5
+FORMAT_NAMES = {FMT_CSR: "csr", FMT_ELL: "ell", FMT_COO: "coo", FMT_HYB: "hyb", FMT_BSR: "bsr", FMT_SELL: "sell"}
 TPR_SPLIT = -1
 (ARR_CSR_ROWPTR, ARR_CSR_COLIDX, ARR_CSR_VALS, ARR_ELL_COLIDX, ARR_ELL_VALS, ARR_COO_ROWS,
- ARR_COO_COLS, ARR_COO_VALS, ARR_BSR_ROWPTR, ARR_BSR_COLIDX, ARR_BSR_VALS, ARR_ELL_PITCH) = range(12)
+ ARR_COO_COLS, ARR_COO_VALS, ARR_BSR_ROWPTR, ARR_BSR_COLIDX, ARR_BSR_VALS, ARR_ELL_PITCH,
+ ARR_SELL_PTR, ARR_SELL_COLIDX, ARR_SELL_VALS, ARR_SELL_PERM) = range(16)
 
 # every entry point include/spmv.h declares (checked by the CPU test suite)
 EXPORTED = ("spmv_config_default", "spmv_create", "spmv_set_config", "spmv_get_config",
             "spmv_get_info", "spmv_run", "spmv_export_bytes", "spmv_export", "spmv_destroy",
             "spmv_last_error", "spmv_coo_run_noalloc", "spmv_features", "spmv_selector_load",
             "spmv_selector_infer", "spmv_select", "spmv_batch_create", "spmv_batch_tune",
-            "spmv_batch_launch", "spmv_batch_get_plan", "spmv_batch_destroy", "spmv_batch_run")
+            "spmv_batch_launch", "spmv_batch_get_plan", "spmv_batch_destroy", "spmv_batch_run",
+            "spmv_select_runtime", "spmv_cg")
 
 
 class SpmvError(RuntimeError):
@@ -48,10 +50,32 @@ class spmv_config(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class spmv_runtime_decision(ctypes.Structure):
+    _fields_ = [("convert", ctypes.c_int32), ("current_class", ctypes.c_int32),
+                ("selected_class", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("predicted_us_current", ctypes.c_double), ("predicted_us_selected", ctypes.c_double),
+                ("predicted_pack_us", ctypes.c_double), ("measured_select_us", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
+class spmv_cg_result(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("breakdown", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("rho0", ctypes.c_double), ("rho", ctypes.c_double), ("bb", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+CG_MAX_ITERATIONS = 16777216
+
+
 class spmv_info(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("nnz", ctypes.c_int64),
                 ("max_row", ctypes.c_int64), ("ell_width", ctypes.c_int64),
-                ("hyb_coo_nnz", ctypes.c_int64), ("bsr_blocks", ctypes.c_int64),
+                ("hyb_coo_nnz", ctypes.c_int64), ("bsr_blocks", ctypes.c_int64), ("sell_slots", ctypes.c_int64),
                 ("format_bytes", ctypes.c_int64), ("value_type", ctypes.c_int32),
                 ("format", ctypes.c_int32)]
 
@@ -97,8 +121,11 @@ def load_library(path: str | None = None):
         "spmv_selector_load": (ctypes.c_int, [_VP, _I64]),
         "spmv_selector_infer": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(_I32), _VP]),
         "spmv_select": (ctypes.c_int, [_VP, ctypes.POINTER(spmv_config), _VP, _VP]),
+        "spmv_select_runtime": (ctypes.c_int, [_VP, _I64, ctypes.POINTER(spmv_config),
+                                               ctypes.POINTER(spmv_runtime_decision), _VP]),
         "spmv_coo_run_noalloc": (ctypes.c_int, [_I64, _I64, _I64, _VP, _VP, _VP, _I32, _D, _VP, _D, _VP,
                                                 _VP]),
+        "spmv_cg": (ctypes.c_int, [_VP, _VP, _VP, _D, _I32, _VP, ctypes.POINTER(spmv_cg_result), _VP]),
         "spmv_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -276,6 +303,25 @@ def spmv_batch_destroy(b: int):
 def spmv_batch_run(handles, alphas, xs, betas, ys, stream=None):
     n, hs, al, be, xp, yp = _batch_arrays(handles, alphas, xs, betas, ys)
     _check(load_library().spmv_batch_run(hs, n, al.ctypes.data, xp, be.ctypes.data, yp, _stream(stream)))
+
+
+def spmv_select_runtime(h: int, expected_runs: int, stream=None):
+    """(chosen spmv_config, spmv_runtime_decision) for the handle's matrix."""
+    cfg = spmv_config()
+    dec = spmv_runtime_decision()
+    _check(load_library().spmv_select_runtime(h, int(expected_runs), ctypes.byref(cfg), ctypes.byref(dec),
+                                              _stream(stream)))
+    return cfg, dec
+
+
+def spmv_cg(h: int, b, x, tol: float, maxit: int, rho=None, stream=None) -> spmv_cg_result:
+    """Conjugate gradients on the handle's matrix: x (device tensor) holds x_0
+    on entry and the last iterate on return; rho (optional float64 device
+    tensor of maxit + 1 entries) receives r_k.r_k per iteration."""
+    out = spmv_cg_result()
+    _check(load_library().spmv_cg(h, _ptr(b), _ptr(x), float(tol), int(maxit), _ptr(rho), ctypes.byref(out),
+                                  _stream(stream)))
+    return out
 
 
 NOALLOC_MAX_NNZ = 1 << 25

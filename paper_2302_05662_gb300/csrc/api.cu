@@ -70,10 +70,6 @@ int apply_carveout(const void *kernel, int carveout) {
     return SPMV_OK;
 }
 
-namespace {
-
-bool pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
-
 // default threads per row: the largest power of two (1..32) that leaves each
 // lane at least eight entries of a mean-length row, so lanes accumulate
 // sequentially and the cross-lane adds (costly in fp64 on this GPU) are few
@@ -84,10 +80,16 @@ int default_tpr(const spmv_matrix *h) {
     return t;
 }
 
+namespace {
+
+bool pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
+
 // Loads in flight per thread: ELL (and the ELL part of HYB) keeps four
 // column/value pairs in flight (measured fastest on regular matrices), the
 // other kernels two (or 8 entries per lane for the chunked kernels).
-int default_unroll(int format) { return format == SPMV_FMT_ELL || format == SPMV_FMT_HYB ? 4 : 2; }
+int default_unroll(int format) {
+    return format == SPMV_FMT_ELL || format == SPMV_FMT_HYB || format == SPMV_FMT_SELL ? 4 : 2;
+}
 
 // Fills defaults and validates; returns SPMV_ERR_INVALID on a bad field.
 int resolve_config(const spmv_matrix *h, const spmv_config *in, spmv_config *out) {
@@ -100,7 +102,7 @@ int resolve_config(const spmv_matrix *h, const spmv_config *in, spmv_config *out
         if (c.regcap == 0) c.regcap = 64;
         if (c.bsr_block == 0) c.bsr_block = 4;
     }
-    if (c.format < SPMV_FMT_CSR || c.format > SPMV_FMT_BSR) {
+    if (c.format < SPMV_FMT_CSR || c.format > SPMV_FMT_SELL) {
         set_error("config: unknown format %d", c.format);
         return SPMV_ERR_INVALID;
     }
@@ -108,8 +110,9 @@ int resolve_config(const spmv_matrix *h, const spmv_config *in, spmv_config *out
         set_error("config: threads_per_block %d is not a power of two in [32, 1024]", c.threads_per_block);
         return SPMV_ERR_INVALID;
     }
-    if (c.unroll != 1 && c.unroll != 2 && c.unroll != 4) {
-        set_error("config: unroll %d not in {1, 2, 4}", c.unroll);
+    const bool ell_family = c.format == SPMV_FMT_ELL || c.format == SPMV_FMT_HYB || c.format == SPMV_FMT_SELL;
+    if (c.unroll != 1 && c.unroll != 2 && c.unroll != 4 && !(c.unroll == 8 && ell_family)) {
+        set_error("config: unroll %d not in {1, 2, 4} (8 also for ELL, HYB, SELL)", c.unroll);
         return SPMV_ERR_INVALID;
     }
     if (c.regcap != 32 && c.regcap != 64) {
@@ -145,7 +148,7 @@ int resolve_config(const spmv_matrix *h, const spmv_config *in, spmv_config *out
         break;
     default:
         if (c.threads_per_row != 0 && c.threads_per_row != 1) {
-            set_error("config: threads_per_row must be 0 or 1 for ELL, COO and HYB");
+            set_error("config: threads_per_row must be 0 or 1 for ELL, COO, HYB and SELL");
             return SPMV_ERR_INVALID;
         }
         c.threads_per_row = 1;
@@ -164,6 +167,7 @@ int runner(const spmv_matrix *h, int kind, double alpha, const void *x, double b
 }
 
 void destroy_all(spmv_matrix *h) {
+    free_cg(h);
     free_packed(h);
     if (h->rowptr) cudaFree(h->rowptr);
     if (h->colidx) cudaFree(h->colidx);
@@ -173,6 +177,23 @@ void destroy_all(spmv_matrix *h) {
 }
 
 }  // namespace
+
+int run_product(const spmv_matrix *h, double alpha, const void *x, double beta, void *y, cudaStream_t s) {
+    if (h->nnz == 0) return runner(h, RUN_SCALE, alpha, x, beta, y, s);
+    switch (h->cfg.format) {
+    case SPMV_FMT_CSR:
+        return runner(h, h->cfg.threads_per_row == SPMV_TPR_SPLIT ? RUN_CSR_SPLIT : RUN_CSR_VECTOR, alpha, x, beta, y,
+                      s);
+    case SPMV_FMT_ELL: return runner(h, RUN_ELL, alpha, x, beta, y, s);
+    case SPMV_FMT_COO: return runner(h, RUN_COO, alpha, x, beta, y, s);
+    case SPMV_FMT_HYB: return runner(h, RUN_HYB, alpha, x, beta, y, s);
+    case SPMV_FMT_BSR: return runner(h, RUN_BSR, alpha, x, beta, y, s);
+    case SPMV_FMT_SELL: return runner(h, RUN_SELL, alpha, x, beta, y, s);
+    }
+    set_error("spmv_run: bad format");
+    return SPMV_ERR_INVALID;
+}
+
 }  // namespace spmv
 
 using namespace spmv;
@@ -319,6 +340,10 @@ int spmv_get_info(spmv_handle h, spmv_info *out) {
         out->bsr_blocks = h->bsr_blocks;
         out->format_bytes = h->bsr_blocks * (vs * h->bsr_r * h->bsr_r + 4) + 4 * (h->bsr_mb + 1);
         break;
+    case SPMV_FMT_SELL:
+        out->sell_slots = h->sell_slots;
+        out->format_bytes = h->sell_slots * (vs + 4) + 4 * (h->sell_nslices + 1) + 4 * h->m;
+        break;
     }
     return SPMV_OK;
 }
@@ -333,19 +358,7 @@ int spmv_run(spmv_handle h, double alpha, const void *d_x, double beta, void *d_
         return SPMV_ERR_INVALID;
     }
     if (h->m == 0) return SPMV_OK;
-    cudaStream_t s = (cudaStream_t)stream;
-    if (h->nnz == 0) return runner(h, RUN_SCALE, alpha, d_x, beta, d_y, s);
-    switch (h->cfg.format) {
-    case SPMV_FMT_CSR:
-        return runner(h, h->cfg.threads_per_row == SPMV_TPR_SPLIT ? RUN_CSR_SPLIT : RUN_CSR_VECTOR, alpha, d_x, beta,
-                      d_y, s);
-    case SPMV_FMT_ELL: return runner(h, RUN_ELL, alpha, d_x, beta, d_y, s);
-    case SPMV_FMT_COO: return runner(h, RUN_COO, alpha, d_x, beta, d_y, s);
-    case SPMV_FMT_HYB: return runner(h, RUN_HYB, alpha, d_x, beta, d_y, s);
-    case SPMV_FMT_BSR: return runner(h, RUN_BSR, alpha, d_x, beta, d_y, s);
-    }
-    set_error("spmv_run: bad format");
-    return SPMV_ERR_INVALID;
+    return run_product(h, alpha, d_x, beta, d_y, (cudaStream_t)stream);
 }
 
 namespace {
@@ -386,6 +399,18 @@ int array_of(spmv_handle h, int32_t id, const void **ptr, int64_t *bytes) {
         if (h->bsr_val) { *ptr = h->bsr_val; *bytes = vs * h->bsr_blocks * h->bsr_r * h->bsr_r; }
         break;
     case SPMV_ARR_ELL_PITCH: *bytes = h->ell_pitch; break;
+    case SPMV_ARR_SELL_PTR:
+        if (h->sell_ptr) { *ptr = h->sell_ptr; *bytes = 4 * (h->sell_nslices + 1); }
+        break;
+    case SPMV_ARR_SELL_COLIDX:
+        if (h->sell_col) { *ptr = h->sell_col; *bytes = 4 * h->sell_slots; }
+        break;
+    case SPMV_ARR_SELL_VALS:
+        if (h->sell_val) { *ptr = h->sell_val; *bytes = vs * h->sell_slots; }
+        break;
+    case SPMV_ARR_SELL_PERM:
+        if (h->sell_perm) { *ptr = h->sell_perm; *bytes = 4 * h->m; }
+        break;
     default:
         set_error("spmv_export: unknown array id %d", id);
         return SPMV_ERR_INVALID;

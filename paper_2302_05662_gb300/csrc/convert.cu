@@ -521,6 +521,74 @@ __global__ void k_long_fill(const int *rowptr, int64_t nrows, int64_t threshold,
     }
 }
 
+// SELL: sort key per row = descending length (the sort is stable, so rows of
+// equal length keep their order)
+__global__ void k_sell_keys(const int *rowptr, int64_t m, uint64_t *keys, uint32_t *idx) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < m; r += stride) {
+        const int len = rowptr[r + 1] - rowptr[r];
+        keys[r] = (uint64_t)(uint32_t)(0x7fffffff - len);
+        idx[r] = (uint32_t)r;
+    }
+}
+
+// slice width = length of its first (longest) sorted row; slots = 32 * width
+__global__ void k_sell_widths(const int *rowptr, const uint32_t *perm, int64_t m, int64_t nslices, int *slots) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t sl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; sl < nslices; sl += stride) {
+        const uint32_t r = perm[sl * 32];
+        slots[sl] = 32 * (rowptr[r + 1] - rowptr[r]);
+    }
+}
+
+template <typename V>
+__global__ void k_sell_fill(const int *rowptr, const int *colidx, const V *vals, const uint32_t *perm, int64_t m,
+                            int64_t nslices, const int *sptr, int *scol, V *sval, int *sperm) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nslices * 32; p += stride) {
+        const int64_t sl = p / 32, lane = p % 32;
+        const int64_t base = sptr[sl], width = (sptr[sl + 1] - base) / 32;
+        int64_t rs = 0, len = 0;
+        if (p < m) {
+            const uint32_t r = perm[p];
+            sperm[p] = (int)r;
+            rs = rowptr[r];
+            len = rowptr[r + 1] - rs;
+        }
+        for (int64_t k = 0; k < width; ++k) {
+            const bool have = k < len;
+            scol[base + 32 * k + lane] = have ? colidx[rs + k] : -1;
+            sval[base + 32 * k + lane] = have ? vals[rs + k] : V(0.0f);
+        }
+    }
+}
+
+// work items per slice: ceil(width / kmax), at least one
+__global__ void k_sell_item_count(const int *sptr, int64_t nslices, int kmax, int *cnt) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t sl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; sl < nslices; sl += stride) {
+        const int width = (sptr[sl + 1] - sptr[sl]) / 32;
+        cnt[sl] = width == 0 ? 1 : (width + kmax - 1) / kmax;
+    }
+}
+
+__global__ void k_sell_item_fill(const int *sptr, int64_t nslices, int kmax, const int *off, int *it_slice,
+                                 int *it_k0, int *it_k1, int *it_c0, int *it_c1) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t sl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; sl < nslices; sl += stride) {
+        const int width = (sptr[sl + 1] - sptr[sl]) / 32;
+        const int n = width == 0 ? 1 : (width + kmax - 1) / kmax;
+        const int o = off[sl];
+        for (int j = 0; j < n; ++j) {
+            it_slice[o + j] = (int)sl;
+            it_k0[o + j] = j * kmax;
+            it_k1[o + j] = min((j + 1) * kmax, width);
+            it_c0[o + j] = o;
+            it_c1[o + j] = o + n - 1;
+        }
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -685,6 +753,11 @@ void free_packed(spmv_matrix *h) {
     f(h->bsr_rowptr); h->bsr_rowptr = nullptr;
     f(h->bsr_col); h->bsr_col = nullptr;
     f(h->bsr_val); h->bsr_val = nullptr;
+    f(h->sell_ptr); h->sell_ptr = nullptr;
+    f(h->sell_col); h->sell_col = nullptr;
+    f(h->sell_val); h->sell_val = nullptr;
+    f(h->sell_perm); h->sell_perm = nullptr;
+    h->sell_nslices = h->sell_slots = 0;
     h->bsr_r = 0;
     h->bsr_mb = h->bsr_blocks = 0;
     f(h->seg.meta0); f(h->seg.meta1);
@@ -840,6 +913,84 @@ int pack_bsr(spmv_matrix *h, int r, cudaStream_t s) {
 
 }  // namespace
 
+namespace {
+constexpr int SELL_KMAX = 256;  // slice entries per work item
+
+int pack_sell(spmv_matrix *h, cudaStream_t s) {
+    const int64_t m = h->m;
+    const int64_t nslices = (m + 31) / 32;
+    const size_t vs = value_size(h->vt);
+    h->sell_nslices = nslices;
+    SPMV_TRY(dalloc(&h->sell_ptr, (size_t)nslices + 1));
+    SPMV_TRY(dalloc(&h->sell_perm, (size_t)std::max<int64_t>(m, 1)));
+    if (m == 0) {
+        SPMV_CUDA_TRY(cudaMemsetAsync(h->sell_ptr, 0, sizeof(int), s));
+        SPMV_TRY(dalloc(&h->sell_col, 1));
+        SPMV_TRY(dalloc_bytes(&h->sell_val, vs));
+        h->sell_slots = 0;
+        return SPMV_OK;
+    }
+    // sort all rows by descending length (stable): slices group rows of
+    // similar length, so padding stays small even for power-law rows
+    Tmp<uint64_t> k0, k1;
+    Tmp<uint32_t> v0, v1;
+    SPMV_TRY(k0.alloc(m, s));
+    SPMV_TRY(k1.alloc(m, s));
+    SPMV_TRY(v0.alloc(m, s));
+    SPMV_TRY(v1.alloc(m, s));
+    k_sell_keys<<<grid1d(m, 256), 256, 0, s>>>(h->rowptr, m, k0.p, v0.p);
+    uint64_t *ks;
+    uint32_t *perm;
+    SPMV_TRY(radix_sort_pairs(k0.p, v0.p, k1.p, v1.p, m, 32, s, &ks, &perm));
+    Tmp<int> slots;
+    SPMV_TRY(slots.alloc(nslices + 1, s));
+    SPMV_CUDA_TRY(cudaMemsetAsync(slots.p, 0, sizeof(int) * (nslices + 1), s));
+    k_sell_widths<<<grid1d(nslices, 256), 256, 0, s>>>(h->rowptr, perm, m, nslices, slots.p);
+    int64_t total = 0;
+    SPMV_TRY(exclusive_scan(slots.p, h->sell_ptr, nslices + 1, s, &total));
+    if ((double)total > 8.0 * (double)h->nnz + (double)(1 << 24)) {
+        set_error("SELL: %lld padded slots exceed 8 x nnz + 2^24", (long long)total);
+        return SPMV_ERR_UNSUPPORTED;
+    }
+    h->sell_slots = total;
+    SPMV_TRY(dalloc(&h->sell_col, (size_t)total));
+    SPMV_TRY(dalloc_bytes(&h->sell_val, vs * total));
+    const unsigned g = grid1d(nslices * 32, 256);
+    if (h->vt == SPMV_F64)
+        k_sell_fill<double><<<g, 256, 0, s>>>(h->rowptr, h->colidx, (const double *)h->vals, perm, m, nslices,
+                                              h->sell_ptr, h->sell_col, (double *)h->sell_val, h->sell_perm);
+    else if (h->vt == SPMV_F32)
+        k_sell_fill<float><<<g, 256, 0, s>>>(h->rowptr, h->colidx, (const float *)h->vals, perm, m, nslices,
+                                             h->sell_ptr, h->sell_col, (float *)h->sell_val, h->sell_perm);
+    else
+        k_sell_fill<__nv_bfloat16><<<g, 256, 0, s>>>(h->rowptr, h->colidx, (const __nv_bfloat16 *)h->vals, perm, m,
+                                                     nslices, h->sell_ptr, h->sell_col,
+                                                     (__nv_bfloat16 *)h->sell_val, h->sell_perm);
+    SPMV_CUDA_TRY(cudaGetLastError());
+    // work items (slice, k range) and the partials joining a slice's items
+    LongRows &L = h->lng;
+    Tmp<int> cnt, off;
+    SPMV_TRY(cnt.alloc(nslices, s));
+    SPMV_TRY(off.alloc(nslices, s));
+    k_sell_item_count<<<grid1d(nslices, 256), 256, 0, s>>>(h->sell_ptr, nslices, SELL_KMAX, cnt.p);
+    int64_t nitems = 0;
+    SPMV_TRY(exclusive_scan(cnt.p, off.p, nslices, s, &nitems));
+    L.nseg = nitems;
+    L.threshold = SELL_KMAX;
+    SPMV_TRY(dalloc(&L.seg_row, (size_t)nitems));
+    SPMV_TRY(dalloc(&L.seg_begin, (size_t)nitems));
+    SPMV_TRY(dalloc(&L.seg_end, (size_t)nitems));
+    SPMV_TRY(dalloc(&L.seg_c0, (size_t)nitems));
+    SPMV_TRY(dalloc(&L.seg_c1, (size_t)nitems));
+    k_sell_item_fill<<<grid1d(nslices, 256), 256, 0, s>>>(h->sell_ptr, nslices, SELL_KMAX, off.p, L.seg_row,
+                                                           L.seg_begin, L.seg_end, L.seg_c0, L.seg_c1);
+    SPMV_CUDA_TRY(cudaGetLastError());
+    SPMV_TRY(alloc_partials(&L.part, nitems, 32, h->vt, s));
+    SPMV_CUDA_TRY(cudaStreamSynchronize(s));
+    return SPMV_OK;
+}
+}  // namespace
+
 int build_split_meta(const int32_t *rowptr, int64_t m, int64_t nnz, int C, int32_t *meta0, cudaStream_t s) {
     const int64_t nchunks = (nnz + C - 1) / C;
     if (m == 0) return SPMV_OK;
@@ -877,6 +1028,8 @@ int ensure_seg_scratch(spmv_matrix *h, int items, bool split_csr, cudaStream_t s
 }
 
 int pack_format(spmv_matrix *h, const spmv_config &cfg, cudaStream_t s) {
+    // a solver graph captured the old launches
+    free_cg(h);
     // a change of launch parameters only (block size, register cap, carveout)
     // keeps the packed arrays
     const spmv_config &p = h->packed_req;
@@ -891,7 +1044,7 @@ int pack_format(spmv_matrix *h, const spmv_config &cfg, cudaStream_t s) {
     h->packed = false;
     h->packed_req = cfg;
     h->cfg = cfg;
-    const int items = 4 * cfg.unroll;
+    const int items = 4 * (cfg.unroll > 4 ? 4 : cfg.unroll);  // COO parts: at most 16 entries per lane
     switch (cfg.format) {
     case SPMV_FMT_CSR:
         if (cfg.threads_per_row == SPMV_TPR_SPLIT) {
@@ -927,6 +1080,9 @@ int pack_format(spmv_matrix *h, const spmv_config &cfg, cudaStream_t s) {
         SPMV_TRY(ensure_seg_scratch(h, items, false, s));
         break;
     }
+    case SPMV_FMT_SELL:
+        SPMV_TRY(pack_sell(h, s));
+        break;
     case SPMV_FMT_BSR: {
         SPMV_TRY(pack_bsr(h, cfg.bsr_block, s));
         const int64_t thr = 256LL * cfg.threads_per_row;

@@ -246,6 +246,10 @@ struct LongRows {
 
 }  // namespace spmv
 
+namespace spmv {
+struct CgPlan;
+}
+
 struct spmv_matrix {
     int64_t m = 0, n = 0, nnz = 0, max_row = 0;
     int32_t vt = SPMV_F64;
@@ -272,10 +276,17 @@ struct spmv_matrix {
     int64_t bsr_mb = 0, bsr_blocks = 0;
     int32_t *bsr_rowptr = nullptr, *bsr_col = nullptr;
     void *bsr_val = nullptr;
+    // SELL: 32-row slices, column-major inside a slice, all rows stably
+    // sorted by descending length; work items = (slice, k range)
+    int64_t sell_nslices = 0, sell_slots = 0;
+    int32_t *sell_ptr = nullptr, *sell_col = nullptr, *sell_perm = nullptr;
+    void *sell_val = nullptr;
     // scratch of the segmented-reduction kernels (COO, HYB tail, split CSR)
     spmv::SegScratch seg;
     // deferred long rows of vector CSR and BSR
     spmv::LongRows lng;
+    // conjugate-gradient plan (cg.cu): scratch vectors and the solve's graph
+    spmv::CgPlan *cg = nullptr;
 };
 
 namespace spmv {
@@ -294,14 +305,22 @@ void free_partials(Partials *p);
 int build_long_rows(spmv_matrix *h, const int32_t *rowptr, int64_t nrows, int64_t threshold, int64_t seg,
                     int stride, cudaStream_t s);
 
+// y = alpha A x + beta y in the handle's current format (api.cu)
+int run_product(const spmv_matrix *h, double alpha, const void *x, double beta, void *y, cudaStream_t s);
+// release the conjugate-gradient plan (cg.cu); packs it captured go stale on re-pack
+void free_cg(spmv_matrix *h);
+
 // kernel launchers: one runner per value type (kernels_<type>.cu)
-enum RunKind { RUN_CSR_VECTOR, RUN_CSR_SPLIT, RUN_ELL, RUN_COO, RUN_HYB, RUN_BSR, RUN_SCALE };
+enum RunKind { RUN_CSR_VECTOR, RUN_CSR_SPLIT, RUN_ELL, RUN_COO, RUN_HYB, RUN_BSR, RUN_SCALE, RUN_SELL };
 int run_kernels_f64(int kind, const spmv_matrix *h, double alpha, const void *x, double beta, void *y,
                     cudaStream_t s);
 int run_kernels_f32(int kind, const spmv_matrix *h, double alpha, const void *x, double beta, void *y,
                     cudaStream_t s);
 int run_kernels_bf16(int kind, const spmv_matrix *h, double alpha, const void *x, double beta, void *y,
                      cudaStream_t s);
+
+// default lanes per row of vector CSR for this matrix (api.cu)
+int default_tpr(const spmv_matrix *h);
 
 // launch helpers (api.cu)
 int resident_blocks(const void *kernel, int threads);

@@ -129,8 +129,8 @@ k_csr_long(int64_t nseg, const int *__restrict__ seg_row, const int *__restrict_
 // Index matrices).  Padding has column -1 and rows are left-packed, so a
 // thread stops at its first padding slot and reads no padding values.
 // ---------------------------------------------------------------------------
-template <typename V, typename T, int UNROLL>
-__global__ void __launch_bounds__(1024)
+template <typename V, typename T, int UNROLL, int REGCAP>
+__global__ void __launch_bounds__(1024) __maxnreg__(REGCAP)
 k_ell(int64_t m, int64_t width, int64_t pitch, const int *__restrict__ col, const V *__restrict__ val,
       const T *__restrict__ x, T *__restrict__ y, T alpha, T beta) {
     const Epi<T> ep(alpha, beta);
@@ -140,12 +140,20 @@ k_ell(int64_t m, int64_t width, int64_t pitch, const int *__restrict__ col, cons
         int64_t k = 0;
         bool done = false;
         for (; !done && k + UNROLL <= width; k += UNROLL) {
+            // all loads of the group go out together: padding slots hold a
+            // zero value and column -1 (gathered at column 0, not added)
             int c[UNROLL];
+            T v[UNROLL], xv[UNROLL];
 #pragma unroll
             for (int u = 0; u < UNROLL; ++u) c[u] = ld_s(col + (k + u) * pitch + r);
 #pragma unroll
             for (int u = 0; u < UNROLL; ++u) {
-                if (c[u] >= 0) acc += ld_val(val + (k + u) * pitch + r) * ld_x(x, c[u]);
+                v[u] = ld_val(val + (k + u) * pitch + r);
+                xv[u] = ld_x(x, c[u] >= 0 ? c[u] : 0);
+            }
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) {
+                if (c[u] >= 0) acc = fma(v[u], xv[u], acc);
                 else done = true;
             }
         }
@@ -287,6 +295,59 @@ k_bsr_long(int64_t nseg, const int *__restrict__ seg_row, const int *__restrict_
             }
         }
         __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// SELL (Section 2.3: slices of rows stored as small ELL matrices with a slice
+// pointer array).  Slices are 32 rows -- one warp, one lane per row -- of
+// rows sorted by descending length, so a slice's rows have similar lengths
+// and little padding.  A work item is (slice, k range): a
+// slice wider than 256 entries becomes several items whose per-row partials
+// are joined in item order, so a slice of power-law rows is not left to one
+// warp.
+// ---------------------------------------------------------------------------
+template <typename V, typename T, int UNROLL, int REGCAP>
+__global__ void __launch_bounds__(1024) __maxnreg__(REGCAP)
+k_sell(int64_t m, int64_t nitems, const int *__restrict__ it_slice, const int *__restrict__ it_k0,
+       const int *__restrict__ it_k1, const int *__restrict__ it_c0, const int *__restrict__ it_c1,
+       const int *__restrict__ sptr, const int *__restrict__ col, const V *__restrict__ val,
+       const int *__restrict__ perm, const T *__restrict__ x, T *__restrict__ y, T alpha, T beta,
+       const PartialsT<T> P) {
+    const Epi<T> ep(alpha, beta);
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t it = warp; it < nitems; it += nwarps) {
+        const int sl = __ldg(it_slice + it), k0 = __ldg(it_k0 + it), k1 = __ldg(it_k1 + it);
+        const int64_t base = (int64_t)__ldg(sptr + sl) + lane;
+        T acc = T(0);
+        int k = k0;
+        for (; k + UNROLL <= k1; k += UNROLL) {
+            int c[UNROLL];
+            T v[UNROLL], xv[UNROLL];
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) c[u] = ld_s(col + base + 32LL * (k + u));
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) {
+                v[u] = ld_val(val + base + 32LL * (k + u));
+                xv[u] = ld_x(x, c[u] >= 0 ? c[u] : 0);
+            }
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u)
+                if (c[u] >= 0) acc = fma(v[u], xv[u], acc);
+        }
+        for (; k < k1; ++k) {
+            const int c = ld_s(col + base + 32LL * k);
+            if (c >= 0) acc = fma(ld_val(val + base + 32LL * k), ld_x(x, c), acc);
+        }
+        const int64_t p = (int64_t)sl * 32 + lane;
+        if (p < m) {
+            const int row = __ldg(perm + p);
+            const int64_t c0 = __ldg(it_c0 + it), c1 = __ldg(it_c1 + it);
+            T total = acc;
+            if (c0 == c1 || join_partial<T>(it, c0, c1, lane, acc, P, &total)) ep.store(y, row, total);
+        }
     }
 }
 

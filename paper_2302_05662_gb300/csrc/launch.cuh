@@ -96,15 +96,21 @@ int run_csr_vector_vt(const spmv_matrix *h, double alpha, const void *x, double 
 }
 
 // ----------------------------------- ELL -----------------------------------
-template <typename V, typename T, int U>
-int launch_ell(const spmv_matrix *h, int64_t width, T alpha, const T *x, T beta, T *y, cudaStream_t s) {
-    auto kern = k_ell<V, T, U>;
+template <typename V, typename T, int U, int RC>
+int launch_ell_rc(const spmv_matrix *h, int64_t width, T alpha, const T *x, T beta, T *y, cudaStream_t s) {
+    auto kern = k_ell<V, T, U, RC>;
     const int tpb = h->cfg.threads_per_block;
     SPMV_TRY(apply_carveout((const void *)kern, h->cfg.carveout));
     const int grid = wave_grid((const void *)kern, tpb, (h->m + tpb - 1) / tpb, h->sm_count);
     kern<<<grid, tpb, 0, s>>>(h->m, width, h->ell_pitch, h->ell_col, (const V *)h->ell_val, x, y, alpha, beta);
     SPMV_LAUNCH_CHECK();
     return SPMV_OK;
+}
+
+template <typename V, typename T, int U>
+int launch_ell(const spmv_matrix *h, int64_t width, T alpha, const T *x, T beta, T *y, cudaStream_t s) {
+    return h->cfg.regcap == 32 ? launch_ell_rc<V, T, U, 32>(h, width, alpha, x, beta, y, s)
+                               : launch_ell_rc<V, T, U, 64>(h, width, alpha, x, beta, y, s);
 }
 
 template <int VT>
@@ -115,6 +121,7 @@ int run_ell_vt(const spmv_matrix *h, double alpha, const void *x, double beta, v
     switch (h->cfg.unroll) {
     case 1: return launch_ell<V, T, 1>(h, h->ell_width, a, (const T *)x, b, (T *)y, s);
     case 2: return launch_ell<V, T, 2>(h, h->ell_width, a, (const T *)x, b, (T *)y, s);
+    case 8: return launch_ell<V, T, 8>(h, h->ell_width, a, (const T *)x, b, (T *)y, s);
     default: return launch_ell<V, T, 4>(h, h->ell_width, a, (const T *)x, b, (T *)y, s);
     }
 }
@@ -152,6 +159,41 @@ int run_bsr_vt(const spmv_matrix *h, double alpha, const void *x, double beta, v
     const T a = (T)alpha, b = (T)beta;
     if (h->bsr_r == 2) return bsr_s<V, T, 2>(h, a, (const T *)x, b, (T *)y, s);
     return bsr_s<V, T, 4>(h, a, (const T *)x, b, (T *)y, s);
+}
+
+// ----------------------------------- SELL ----------------------------------
+template <typename V, typename T, int U, int RC>
+int launch_sell_rc(const spmv_matrix *h, T alpha, const T *x, T beta, T *y, cudaStream_t s) {
+    auto kern = k_sell<V, T, U, RC>;
+    const int tpb = h->cfg.threads_per_block;
+    SPMV_TRY(apply_carveout((const void *)kern, h->cfg.carveout));
+    const LongRows &L = h->lng;
+    const int64_t wpb = tpb / 32;
+    const int grid = wave_grid((const void *)kern, tpb, (L.nseg + wpb - 1) / wpb, h->sm_count);
+    kern<<<grid, tpb, 0, s>>>(h->m, L.nseg, L.seg_row, L.seg_begin, L.seg_end, L.seg_c0, L.seg_c1, h->sell_ptr,
+                              h->sell_col, (const V *)h->sell_val, h->sell_perm, x, y, alpha, beta,
+                              PartialsT<T>::of(L.part));
+    SPMV_LAUNCH_CHECK();
+    return SPMV_OK;
+}
+
+template <typename V, typename T, int U>
+int launch_sell(const spmv_matrix *h, T alpha, const T *x, T beta, T *y, cudaStream_t s) {
+    return h->cfg.regcap == 32 ? launch_sell_rc<V, T, U, 32>(h, alpha, x, beta, y, s)
+                               : launch_sell_rc<V, T, U, 64>(h, alpha, x, beta, y, s);
+}
+
+template <int VT>
+int run_sell_vt(const spmv_matrix *h, double alpha, const void *x, double beta, void *y, cudaStream_t s) {
+    using V = typename VT_<VT>::V;
+    using T = typename VT_<VT>::T;
+    const T a = (T)alpha, b = (T)beta;
+    switch (h->cfg.unroll) {
+    case 1: return launch_sell<V, T, 1>(h, a, (const T *)x, b, (T *)y, s);
+    case 2: return launch_sell<V, T, 2>(h, a, (const T *)x, b, (T *)y, s);
+    case 8: return launch_sell<V, T, 8>(h, a, (const T *)x, b, (T *)y, s);
+    default: return launch_sell<V, T, 4>(h, a, (const T *)x, b, (T *)y, s);
+    }
 }
 
 // ---------------------------- COO / HYB / split ----------------------------
@@ -243,6 +285,7 @@ int run_scale_y_vt(int64_t m, double beta, void *y, cudaStream_t s) {
         case RUN_HYB: return run_hyb_vt<VT>(h, a, x, b, y, s);                                           \
         case RUN_BSR: return run_bsr_vt<VT>(h, a, x, b, y, s);                                           \
         case RUN_SCALE: return run_scale_y_vt<VT>(h->m, b, y, s);                                        \
+        case RUN_SELL: return run_sell_vt<VT>(h, a, x, b, y, s);                                         \
         }                                                                                                \
         return SPMV_ERR_INVALID;                                                                         \
     }

@@ -43,20 +43,32 @@ def full_config(d: dict) -> list:
     return [int(base[k]) for k in CFG_FIELDS]
 
 
-def make_blob(mu, sigma, W1, b1, W2, b2, labels) -> np.ndarray:
+NFMT = 6   # formats 0..5 in the conversion-cost model
+
+
+def make_blob(mu, sigma, W1, b1, W2, b2, labels, W3=None, b3=None, pack=None) -> np.ndarray:
+    """Float32 blob for spmv_selector_load: version 1 (classifier) or, with
+    W3/b3 (time head, K+1 rows) and pack (NFMT x 3 cost model), version 2."""
     W1 = np.asarray(W1, np.float32)
     W2 = np.asarray(W2, np.float32)
     H, F = W1.shape
     K = W2.shape[0]
-    parts = [np.array([MAGIC, VERSION, F, H, K], np.float32), np.asarray(mu, np.float32),
+    version = 2.0 if W3 is not None else 1.0
+    parts = [np.array([MAGIC, version, F, H, K], np.float32), np.asarray(mu, np.float32),
              np.asarray(sigma, np.float32), W1.reshape(-1), np.asarray(b1, np.float32), W2.reshape(-1),
              np.asarray(b2, np.float32), np.array([full_config(l) for l in labels], np.float32).reshape(-1)]
+    if W3 is not None:
+        W3 = np.asarray(W3, np.float32)
+        assert W3.shape == (K + 1, H)
+        parts += [W3.reshape(-1), np.asarray(b3, np.float32).reshape(K + 1),
+                  np.asarray(pack, np.float32).reshape(NFMT * 3)]
     return np.concatenate(parts)
 
 
 def parse_blob(blob) -> dict:
     b = np.asarray(blob, np.float32)
-    assert b[0] == MAGIC and b[1] == VERSION
+    assert b[0] == MAGIC and b[1] in (1.0, 2.0)
+    version = int(b[1])
     F, H, K = int(b[2]), int(b[3]), int(b[4])
     o = 5
     def take(n):
@@ -70,8 +82,13 @@ def parse_blob(blob) -> dict:
     W2 = take(K * H).reshape(K, H)
     b2 = take(K)
     labels = take(K * 8).reshape(K, 8).astype(np.int64)
+    out = dict(version=version, F=F, H=H, K=K, mu=mu, sigma=sigma, W1=W1, b1=b1, W2=W2, b2=b2, labels=labels)
+    if version == 2:
+        out["W3"] = take((K + 1) * H).reshape(K + 1, H)
+        out["b3"] = take(K + 1)
+        out["pack"] = take(NFMT * 3).reshape(NFMT, 3)
     assert o == b.size
-    return dict(F=F, H=H, K=K, mu=mu, sigma=sigma, W1=W1, b1=b1, W2=W2, b2=b2, labels=labels)
+    return out
 
 
 def load_default_selector(path: str = DEFAULT_BLOB) -> dict:
@@ -170,6 +187,60 @@ def predict(w, X):
     return H @ np.asarray(w["W2"]).T + w["b2"]
 
 
+def hidden(w, X):
+    Z, _, _ = transform(X, w["mu"], w["sigma"])
+    return np.maximum(Z @ np.asarray(w["W1"], np.float64).T + np.asarray(w["b1"], np.float64), 0.0)
+
+
+def train_time_head(w, X, T, D, lam: float = 1e-2):
+    """Ridge regression of log(us per product) on the hidden layer, one row
+    per label class (matrices where the class ran) plus one for default CSR:
+    the regression alternative of Section 5.4 on top of the classifier."""
+    Hh = hidden(w, X)
+    A = np.hstack([Hh, np.ones((Hh.shape[0], 1))])
+    K = T.shape[1]
+    W3 = np.zeros((K + 1, Hh.shape[1]))
+    b3 = np.zeros(K + 1)
+    targets = [T[:, k] for k in range(K)] + [D]
+    for k, t in enumerate(targets):
+        ok = np.isfinite(t) & (t > 0)
+        if ok.sum() < 5:
+            b3[k] = np.log(np.nanmedian(np.where(np.isfinite(t), t, np.nan))) if np.isfinite(t).any() else 0.0
+            continue
+        Ak = A[ok]
+        G = Ak.T @ Ak + lam * np.eye(Ak.shape[1])
+        beta = np.linalg.solve(G, Ak.T @ np.log(t[ok]))
+        W3[k] = beta[:-1]
+        b3[k] = beta[-1]
+    return W3, b3
+
+
+def predict_logt(w, W3, b3, X):
+    return hidden(w, X) @ np.asarray(W3, np.float64).T + np.asarray(b3, np.float64)
+
+
+def fit_pack_model(calib):
+    """Least squares of measured conversion time (us) on [1, nnz, m] per
+    format: the conversion-overhead predictor (Section 5.3 step 3).  `calib`
+    is a list of records {format, nnz, m, us}.  Coefficients are clipped at
+    zero so the model never predicts a negative cost."""
+    P = np.zeros((NFMT, 3))
+    for f in range(NFMT):
+        rs = [r for r in calib if r["format"] == f and r["us"] is not None]
+        if len(rs) < 3:
+            continue
+        A = np.array([[1.0, r["nnz"], r["m"]] for r in rs])
+        y = np.array([r["us"] for r in rs])
+        coef, *_ = np.linalg.lstsq(A, y, rcond=None)
+        P[f] = np.maximum(coef, 0.0)
+    return P
+
+
+def gate_decision(t_cur, t_sel, select_us, pack_us, runs):
+    """Convert iff the gain over `runs` products exceeds the overhead."""
+    return (t_cur - t_sel) * runs > select_us + pack_us
+
+
 def evaluate(choice, T, D):
     """Selector quality: slowdown t(choice)/t(best) per matrix, the fraction
     within 10% of the exhaustive best, and the geometric-mean speedup over
@@ -186,7 +257,9 @@ def evaluate(choice, T, D):
 
 def main():
     """Train on the sweep records (matrices 0-1799), evaluate on 1800-1999,
-    write the blob and a JSON report."""
+    write the blob and a JSON report.  With --calib (conversion-time
+    records) the blob is version 2: time head + conversion-cost model, and
+    the report evaluates the run-time gate on the held-out matrices."""
     import argparse
     from . import sweep
     ap = argparse.ArgumentParser(description="train the selector MLP from sweep records")
@@ -196,6 +269,8 @@ def main():
     ap.add_argument("--hidden", type=int, default=64)
     ap.add_argument("--epochs", type=int, default=3000)
     ap.add_argument("--holdout-start", type=int, default=1800)
+    ap.add_argument("--from-blob", default=None, help="reuse this blob's classifier, fit only the heads")
+    ap.add_argument("--calib", nargs="*", default=None, help="conversion-time records (JSON lines)")
     args = ap.parse_args()
     recs = load_records(args.data)
     labels = sweep.label_space()
@@ -204,9 +279,13 @@ def main():
     ok = np.isfinite(T).any(axis=1) & np.isfinite(D)
     train_m = ok & (ids < args.holdout_start)
     test_m = ok & (ids >= args.holdout_start)
-    w = train(X[train_m], T[train_m], hidden=args.hidden, epochs=args.epochs)
+    if args.from_blob:
+        p = parse_blob(np.fromfile(args.from_blob, dtype=np.float32))
+        w = {k: p[k].astype(np.float64) for k in ("mu", "sigma", "W1", "b1", "W2", "b2")}
+    else:
+        w = train(X[train_m], T[train_m], hidden=args.hidden, epochs=args.epochs)
     report = {"train_matrices": int(train_m.sum()), "heldout_matrices": int(test_m.sum()),
-              "classes": len(labels), "hidden": args.hidden}
+              "classes": len(labels), "hidden": int(np.asarray(w["W1"]).shape[0])}
     for name, msk in (("train", train_m), ("heldout", test_m)):
         if msk.any():
             logits = predict(w, X[msk])
@@ -217,13 +296,72 @@ def main():
             report[name + "_by_family"] = {
                 f: evaluate(choice[fam_arr == f], T[msk][fam_arr == f], D[msk][fam_arr == f])
                 for f in sorted(set(fam_arr))}
-    blob = make_blob(w["mu"], w["sigma"], w["W1"], w["b1"], w["W2"], w["b2"], labels)
+    W3 = b3 = pack = None
+    if args.calib is not None:
+        import gzip
+        calib = []
+        for path in args.calib:
+            with (gzip.open(path, "rt") if path.endswith(".gz") else open(path)) as fh:
+                calib += [json.loads(l) for l in fh if l.strip()]
+        W3, b3 = train_time_head(w, X[train_m], T[train_m], D[train_m])
+        pack = fit_pack_model([c for c in calib if c["matrix"] < args.holdout_start])
+        # time head on held-out matrices: error of the selected class and default CSR
+        lt = predict_logt(w, W3, b3, X[test_m])
+        logits = np.where(np.isfinite(T[test_m]), predict(w, X[test_m]), -np.inf)
+        choice = np.argmax(logits, axis=1)
+        rows = np.arange(choice.size)
+        e_sel = np.abs(lt[rows, choice] - np.log(T[test_m][rows, choice]))
+        e_def = np.abs(lt[:, -1] - np.log(D[test_m]))
+        report["time_head_heldout"] = {"median_abs_log_error_selected": float(np.median(e_sel)),
+                                       "median_abs_log_error_default_csr": float(np.median(e_def)),
+                                       "p90_abs_log_error_selected": float(np.quantile(e_sel, 0.9))}
+        # conversion-cost model on held-out calibration records
+        held = [c for c in calib if c["matrix"] >= args.holdout_start and c["us"] is not None]
+        if held:
+            pred = np.array([pack[c["format"]] @ [1.0, c["nnz"], c["m"]] for c in held])
+            meas = np.array([c["us"] for c in held])
+            ss_res = float(((pred - meas) ** 2).sum())
+            ss_tot = float(((meas - meas.mean()) ** 2).sum())
+            report["pack_model_heldout"] = {"n": len(held), "r2": 1.0 - ss_res / ss_tot,
+                                            "median_abs_rel_error": float(np.median(np.abs(pred - meas) / meas))}
+            # the gate on held-out matrices: predicted vs measured decision
+            by = {}
+            for c in held:
+                by.setdefault(c["matrix"], {})[c["format"]] = c["us"]
+            id_test = ids[test_m]
+            agree = {}
+            for runs in (1, 10, 100, 1000, 10000):
+                hits = tot = 0
+                for i, mid in enumerate(id_test):
+                    if mid not in by:
+                        continue
+                    f = int(labels[choice[i]]["format"])
+                    if f not in by[mid]:
+                        continue
+                    t_def, t_sel = D[test_m][i], T[test_m][i, choice[i]]
+                    truth = gate_decision(t_def, t_sel, 0.0, by[mid][f], runs)
+                    guess = gate_decision(np.exp(lt[i, -1]), np.exp(lt[i, choice[i]]), 0.0,
+                                          pack[f] @ [1.0, by_nnz(recs, mid), by_m(recs, mid)], runs)
+                    hits += int(truth == guess)
+                    tot += 1
+                agree[str(runs)] = hits / tot if tot else None
+            report["gate_agreement_heldout"] = agree
+        report["pack_model_us"] = {str(f): [float(v) for v in pack[f]] for f in range(NFMT)}
+    blob = make_blob(w["mu"], w["sigma"], w["W1"], w["b1"], w["W2"], w["b2"], labels, W3, b3, pack)
     blob.tofile(args.out)
     txt = json.dumps(report, indent=1)
     if args.report:
         with open(args.report, "w") as fh:
             fh.write(txt + "\n")
     print(txt)
+
+
+def by_nnz(recs, mid):
+    return next(r["nnz"] for r in recs if r["matrix"] == mid)
+
+
+def by_m(recs, mid):
+    return next(r["m"] for r in recs if r["matrix"] == mid)
 
 
 if __name__ == "__main__":

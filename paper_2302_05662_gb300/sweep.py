@@ -31,10 +31,14 @@ TPB = (32, 64, 128, 256, 512, 1024)
 CSR_TPR = (1, 2, 4, 8, 16, 32, B.TPR_SPLIT)
 
 
-def label_space(tpb=TPB):
+def label_space(tpb=TPB, include_sell: bool = False):
     """The selector's label space: (format, threads_per_block, threads_per_row)
-    points, each a dict of spmv_config fields."""
+    points, each a dict of spmv_config fields.  The committed selector was
+    trained without SELL (include_sell=False); the benchmark's exhaustive
+    search includes it."""
     out = []
+    if include_sell:
+        out += [dict(format=B.FMT_SELL, threads_per_block=t) for t in tpb]
     for t in tpb:
         for tpr in CSR_TPR:
             out.append(dict(format=B.FMT_CSR, threads_per_block=t, threads_per_row=tpr))
@@ -164,6 +168,42 @@ def generate_dataset_matrix(idx: int, n_lo=1e3, n_hi=2.1e6):
     return fam, matgen.family_matrix(fam, n, seed=20_000 + idx, jitter=True)
 
 
+def calibrate_pack(indices, out_path, reps: int = 3):
+    """Conversion-cost calibration: for dataset matrices `indices`, the wall
+    time of spmv_set_config from default CSR to each format (CSR as the
+    split variant), median of `reps`.  Appends JSON lines {matrix, format,
+    nnz, m, us}."""
+    import torch
+    with open(out_path, "a") as fh:
+        for idx in indices:
+            fam, coo = generate_dataset_matrix(idx)
+            rows, cols, vals = device_matrix(coo)
+            h = B.spmv_create(coo.m, coo.n, rows, cols, vals)
+            del rows, cols, vals
+            try:
+                for f in range(6):
+                    cfg = dict(format=f)
+                    if f == B.FMT_CSR:
+                        cfg["threads_per_row"] = B.TPR_SPLIT
+                    ts = []
+                    for _ in range(reps):
+                        B.spmv_set_config(h, B.make_config(format=B.FMT_CSR))
+                        torch.cuda.synchronize()
+                        t0 = time.perf_counter()
+                        try:
+                            B.spmv_set_config(h, B.make_config(**cfg))
+                        except B.SpmvError:
+                            ts = None
+                            break
+                        ts.append((time.perf_counter() - t0) * 1e6)
+                    us = statistics.median(ts) if ts else None
+                    fh.write(json.dumps({"matrix": idx, "family": fam, "format": f, "nnz": coo.nnz, "m": coo.m,
+                                         "us": us}) + "\n")
+                fh.flush()
+            finally:
+                B.spmv_destroy(h)
+
+
 def main():
     ap = argparse.ArgumentParser(description="exhaustive format/launch sweep")
     ap.add_argument("--start", type=int, default=0)
@@ -172,10 +212,15 @@ def main():
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--n-hi", type=float, default=2.1e6)
     ap.add_argument("--time-budget", type=float, default=1e9, help="seconds; stop cleanly after")
+    ap.add_argument("--calibrate-pack", action="store_true",
+                    help="time format conversions of matrices start..start+count instead")
     args = ap.parse_args()
     from . import build
     build.build()
     B.load_library()
+    if args.calibrate_pack:
+        calibrate_pack(range(args.start, args.start + args.count), args.out)
+        return
     done = set()
     if os.path.exists(args.out):
         with open(args.out) as fh:

@@ -15,6 +15,7 @@ SWEEP_VARIANTS = (
     ("coo", dict(format=B.FMT_COO)),
     ("hyb", dict(format=B.FMT_HYB)),
     ("bsr", dict(format=B.FMT_BSR)),
+    ("sell", dict(format=B.FMT_SELL)),
 )
 
 

@@ -58,7 +58,7 @@ def test_full_size_sweep(oracle, mname):
                 h = create(coo, vt, cfg)
             except B.SpmvError as e:
                 # ELL / BSR padded storage over the limit (R-MAT; BSR also Poisson rows)
-                assert cfg.format in (B.FMT_ELL, B.FMT_BSR) and e.status == -4, str(e)
+                assert cfg.format in (B.FMT_ELL, B.FMT_BSR, B.FMT_SELL) and e.status == -4, str(e)
                 continue
             try:
                 got = run(h, vt, x, m=coo.m)

@@ -120,6 +120,7 @@ LAUNCH_CASES = (
     + [("hyb", dict(unroll=u)) for u in (1, 2, 4)]
     + [("hyb", dict(hyb_ell_width=w)) for w in (1, 3, 100)]
     + [("bsr", dict(bsr_block=r, threads_per_row=s)) for r in (2, 4) for s in (1, 2, 4, 8)]
+    + [("sell", dict(unroll=u)) for u in (1, 2, 4)]
     + [(nm, dict(threads_per_block=t)) for nm in VARIANTS for t in (32, 1024)]
     + [(nm, dict(carveout=cv)) for nm in ("csr", "coo") for cv in (0, 50, 100, -1)]
 )
@@ -308,6 +309,45 @@ def test_format_layouts_decode_to_the_matrix(oracle):
                             got[(br * r + i, int(bci[k]) * r + j)] = bv[k, i, j]
                         else:
                             assert bv[k, i, j] == 0
+        assert got == ref
+
+
+def test_sell_layout_decodes_to_the_matrix():
+    """SELL: 32-row slices, entry k of sorted row p at ptr[s] + 32k + (p % 32),
+    rows sorted by descending length (stable), perm maps a sorted row back
+    to its matrix row, padding -1 / 0 after each row."""
+    import torch
+    for coo in (SMALL["rmat_s14_ef16"], matgen.random_coo(1000, 700, 6000, np.random.default_rng(4)),
+                matgen.Coo(37, 9, np.array([0, 36], np.int32), np.array([1, 8], np.int32), np.array([2.0, 3.0]))):
+        vals = np.random.default_rng(5).integers(-9, 10, coo.nnz).astype(float)
+        ci = matgen.Coo(coo.m, coo.n, coo.rows, coo.cols, vals)
+        ref = {(r, c): v for r, c, v in zip(ci.rows.tolist(), ci.cols.tolist(), ci.vals.tolist())}
+        lens = np.bincount(ci.rows, minlength=ci.m)
+        h = create(ci, B.SPMV_F64, cfg_of("sell"))
+        try:
+            info = B.spmv_get_info(h)
+            ptr = _export(h, B.ARR_SELL_PTR, torch.int32).numpy()
+            col = _export(h, B.ARR_SELL_COLIDX, torch.int32).numpy()
+            val = _export(h, B.ARR_SELL_VALS, torch.float64).numpy()
+            perm = _export(h, B.ARR_SELL_PERM, torch.int32).numpy()
+        finally:
+            B.spmv_destroy(h)
+        assert sorted(perm.tolist()) == list(range(ci.m))
+        pl = lens[perm]
+        assert np.all(np.diff(pl) <= 0)                                 # descending lengths
+        same = np.flatnonzero(np.diff(pl) == 0)
+        assert np.all(perm[same] < perm[same + 1])                      # stable among equal lengths
+        assert info.sell_slots == ptr[-1]
+        got = {}
+        for p in range(ci.m):
+            sl, l = divmod(p, 32)
+            width = (ptr[sl + 1] - ptr[sl]) // 32
+            for k in range(width):
+                c = col[ptr[sl] + 32 * k + l]
+                if c < 0:
+                    assert np.all(col[ptr[sl] + 32 * np.arange(k, width) + l] < 0)
+                    break
+                got[(int(perm[p]), int(c))] = val[ptr[sl] + 32 * k + l]
         assert got == ref
 
 

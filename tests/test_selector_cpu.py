@@ -68,3 +68,43 @@ def test_committed_selector_matches_its_report():
     assert abs(got["within_10pct"] - rep["heldout"]["within_10pct"]) <= 0.01
     assert got["within_10pct"] >= 0.90
     assert got["geomean_speedup_vs_default_csr"] > 1.0
+
+
+def test_blob_v2_roundtrip_and_heads():
+    rng = np.random.default_rng(2)
+    H, K = 8, 5
+    w = dict(mu=rng.normal(size=20), sigma=rng.uniform(1, 2, 20), W1=rng.normal(size=(H, 20)),
+             b1=rng.normal(size=H), W2=rng.normal(size=(K, H)), b2=rng.normal(size=K))
+    W3, b3 = rng.normal(size=(K + 1, H)), rng.normal(size=K + 1)
+    pack = rng.uniform(0, 1, (S.NFMT, 3))
+    labels = [dict(format=k, threads_per_block=64) for k in range(K)]
+    blob = S.make_blob(w["mu"], w["sigma"], w["W1"], w["b1"], w["W2"], w["b2"], labels, W3, b3, pack)
+    p = S.parse_blob(blob)
+    assert p["version"] == 2 and p["W3"].shape == (K + 1, H)
+    assert np.allclose(p["pack"], pack.astype(np.float32))
+    assert blob.size == 5 + 40 + H * 20 + H + K * H + K + 8 * K + (K + 1) * H + (K + 1) + S.NFMT * 3
+
+
+def test_time_head_recovers_a_linear_law():
+    rng = np.random.default_rng(3)
+    X = np.abs(rng.normal(size=(300, 20))) + 1.0
+    w = S.train(X, np.ones((300, 3)) + rng.uniform(0, 1, (300, 3)), hidden=16, epochs=50)
+    Hh = S.hidden(w, X)
+    true_w = rng.normal(size=Hh.shape[1])
+    T = np.exp(np.stack([Hh @ true_w + 1.0, Hh @ (0.5 * true_w) - 1.0, Hh @ true_w * 0 + 2.0], axis=1))
+    D = np.exp(Hh @ true_w + 0.3)
+    W3, b3 = S.train_time_head(w, X, T, D, lam=1e-8)
+    lt = S.predict_logt(w, W3, b3, X)
+    assert np.max(np.abs(lt[:, :3] - np.log(T))) < 1e-5
+    assert np.max(np.abs(lt[:, 3] - np.log(D))) < 1e-5
+
+
+def test_pack_model_fit_and_gate():
+    calib = [{"format": f, "nnz": n, "m": m, "us": 50.0 + 0.002 * n + 0.01 * m + 7 * f}
+             for f in range(S.NFMT) for n, m in ((1e5, 1e4), (5e5, 2e4), (2e6, 3e5), (8e6, 5e5))]
+    P = S.fit_pack_model(calib)
+    assert np.allclose(P[2], [64.0, 0.002, 0.01], rtol=1e-6)
+    # gain (100 - 60) x runs against overhead 1000 + 500: pays off from 38 runs
+    assert not S.gate_decision(100.0, 60.0, 1000.0, 500.0, 37)
+    assert S.gate_decision(100.0, 60.0, 1000.0, 500.0, 38)
+    assert not S.gate_decision(50.0, 60.0, 0.0, 0.0, 10 ** 9)      # never when slower
