@@ -46,6 +46,10 @@ def parse():
     p.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16"])
     p.add_argument("--scale", default="full", choices=["full", "small"])
     p.add_argument("--e2e-steps", type=int, default=20)
+    p.add_argument("--no-cg", action="store_true", help="skip the conjugate-gradient section")
+    p.add_argument("--no-tune", action="store_true",
+                   help="skip the exhaustive search (selector choice only; for launch-list captures)")
+    p.add_argument("--no-energy", action="store_true", help="skip the energy report")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--only", default=None, help="comma-separated matrix names (profiling runs)")
     p.add_argument("--no-batched", action="store_true")
@@ -224,7 +228,7 @@ NAMES = ("stencil27_128^3", "poisson16_2^20", "rmat_s20_ef16", "banded_2^20_w32"
 # reports traffic null.
 NCU_TRAFFIC = {
     ("bsr", "banded_2^20_w32", "f64"): (602.3e6, "profiles/bsr_banded_2p20_w32_f64.md"),
-    ("ell", "stencil27_128^3", "f64"): (693.8e6, "profiles/ell_stencil27_128_f64.md"),
+    ("ell", "stencil27_128^3", "f64"): (694.8e6, "profiles/ell_stencil27_128_f64.md"),
 }
 FMT_KEYS = {0: "csr", 1: "ell", 2: "coo", 3: "hyb", 4: "bsr", 5: "sell"}
 
@@ -327,6 +331,115 @@ def batched_section(B, matgen, torch, count=512, seed=7, steps=20):
                      "vector_matrices": int((modes != 0).sum())}}
 
 
+def cg_section(B, matgen, torch, S, have_v2, tol=1e-8, maxit=5000):
+    """Conjugate gradients (spmv_cg) on the 27-point Laplacian 128^3 (centre
+    26, neighbours -1), fp64, b ~ U[-1, 1]: default CSR against the
+    configuration the run-time gate picks for the expected iteration count,
+    with feature extraction, selection, conversion and the solver graph's
+    construction counted as overhead (Section 7.5's iterative setting)."""
+    coo = matgen.stencil_3d(128, 27, values="laplace")
+    r = torch.from_numpy(coo.rows).cuda()
+    c = torch.from_numpy(coo.cols).cuda()
+    v = torch.from_numpy(coo.vals).cuda()
+    h = B.spmv_create(coo.m, coo.n, r, c, v)
+    del r, c, v
+    b = torch.from_numpy(matgen.dense_vector(coo.m, 77)).cuda()
+    x = torch.zeros(coo.m, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    vec_bytes = 11 * 8 * coo.m          # p.q 2 reads; x, r update 4 reads 2 writes; p update 2 reads 1 write
+    spmv_bytes = byte_model(coo.m, coo.n, coo.nnz, 8, 8)
+
+    def solve():
+        x.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = B.spmv_cg(h, b, x, tol, maxit)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return res, e0.elapsed_time(e1)
+
+    def summary(res, ms):
+        it = max(res.iterations, 1)
+        return {"iterations": res.iterations, "converged": bool(res.converged),
+                "rel_residual": float(np.sqrt(res.rho / res.bb)), "solve_ms": round(ms, 3),
+                "ms_per_iteration": round(ms / it, 4),
+                "gbs_per_iteration": round((spmv_bytes + vec_bytes) * it / (ms * 1e-3) / 1e9, 1)}
+
+    try:
+        t0 = time.perf_counter()
+        solve()                                            # builds the default-CSR solver graph
+        t_first = (time.perf_counter() - t0) * 1e3
+        res_d, ms_d = solve()
+        out = {"matrix": "stencil27_laplace_128^3", "nnz": coo.nnz, "tol": tol, "default_csr": summary(res_d, ms_d)}
+        t0 = time.perf_counter()
+        if have_v2:
+            cfg, dec = B.spmv_select_runtime(h, res_d.iterations)
+            out["gate"] = dec.as_dict()
+            convert = bool(dec.convert)
+        else:
+            cfg, _ = B.spmv_select(h)
+            convert = True
+        t_select = (time.perf_counter() - t0) * 1e3
+        t0 = time.perf_counter()
+        if convert:
+            B.spmv_set_config(h, cfg)
+        torch.cuda.synchronize()
+        t_convert = (time.perf_counter() - t0) * 1e3
+        t0 = time.perf_counter()
+        solve()                                            # builds the selected configuration's graph
+        t_first_sel = (time.perf_counter() - t0) * 1e3
+        res_s, ms_s = solve()
+        applied = B.spmv_get_config(h)
+        out["selected"] = dict(summary(res_s, ms_s), config=fmt_name(
+            {k: getattr(applied, k) for k, _ in applied._fields_}))
+        over = t_select + t_convert + max(0.0, t_first_sel - ms_s)
+        out["overhead_ms"] = {"features_and_select": round(t_select, 3), "convert": round(t_convert, 3),
+                              "solver_graph": round(max(0.0, t_first_sel - ms_s), 3),
+                              "default_solver_graph": round(max(0.0, t_first - ms_d), 3)}
+        gain_it = out["default_csr"]["ms_per_iteration"] - out["selected"]["ms_per_iteration"]
+        out["break_even_iterations"] = round(over / gain_it, 1) if gain_it > 0 else None
+        out["end_to_end_speedup"] = round(ms_d / (ms_s + over), 3)
+    finally:
+        B.spmv_destroy(h)
+    return out
+
+
+def energy_section(B, torch, mats, gpu_index, seconds=0.3):
+    """Report-only energy objective (Section 6.3): for every matrix, the best
+    configuration of each format (from the exhaustive search) replayed for
+    `seconds` with the GPU's energy counter read around the loop.  Which
+    format minimises energy is compared with the one that minimises time."""
+    from paper_2302_05662_gb300 import energy
+    try:
+        nv = energy.Nvml(gpu_index)
+    except (OSError, energy.NvmlError) as e:
+        return {"unavailable": str(e)}
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    rows = []
+    try:
+        for p in mats:
+            by = {}
+            for fname, (cfg, t) in sorted(p["per_fmt"].items()):
+                B.spmv_set_config(p["h"], B.make_config(**cfg))
+                r = energy.measure(nv, lambda: B.spmv_run(p["h"], 1.0, p["x"], 0.0, p["y"], sh),
+                                   torch.cuda.synchronize, 2.0 * p["nnz"], min_seconds=seconds)
+                if r:
+                    by[fname] = {"us": round(t, 2), "watts": r["watts"], "gflop_per_joule": r["gflop_per_joule"],
+                                 "uj_per_product": round(r["joules_per_call"] * 1e6, 2)}
+            B.spmv_set_config(p["h"], B.make_config(**p["cfg"]))
+            if by:
+                rows.append({"matrix": p["matrix"], "by_format": by,
+                             "time_best": min(by, key=lambda f: by[f]["us"]),
+                             "energy_best": max(by, key=lambda f: by[f]["gflop_per_joule"])})
+    finally:
+        nv.close()
+    return {"per_matrix": rows, "same_choice": sum(r["time_best"] == r["energy_best"] for r in rows),
+            "matrices": len(rows), "seconds_per_point": seconds,
+            "note": "report-only: one GPU of a shared machine; NVML total-energy counter, read only"}
+
+
 def ours(args, world, rank, local):
     import torch
     import torch.distributed as dist
@@ -346,8 +459,11 @@ def ours(args, world, rank, local):
     vsz = {"f64": 8, "f32": 4, "bf16": 2}[args.dtype]
     xsz = 8 if vt == B.SPMV_F64 else 4
     have_selector = os.path.exists(S.DEFAULT_BLOB)
+    have_v2 = have_selector and S.default_is_v2()
     if have_selector:
         S.load_default_selector()
+    if args.no_tune and not have_selector:
+        raise SystemExit("--no-tune needs the trained selector")
     timer = sweep.Timer()
 
     only = set(args.only.split(",")) if args.only else None
@@ -378,6 +494,8 @@ def ours(args, world, rank, local):
             B.spmv_set_config(h, B.make_config(**fixed))
             t = timer.time_us(h, x, y, reps=3)
             best_cfg, best_t, per_fmt = fixed, t, {fmt_name(fixed): (fixed, t)}
+        elif args.no_tune:
+            best_cfg, best_t, per_fmt = None, None, {}
         else:
             best_cfg, best_t, per_fmt = tune_matrix(B, sweep, h, coo, x, y, timer, reps=5)
         for fname, (cfg, t) in sorted(per_fmt.items()):
@@ -390,6 +508,18 @@ def ours(args, world, rank, local):
         t_sel = t_pack = None
         if have_selector and not args.fixed:
             B.spmv_set_config(h, B.make_config(format=B.FMT_CSR))
+            gate = None
+            if have_v2:
+                # run-time gate from default CSR: predictions against measurements
+                t_def = timer.time_us(h, x, y, reps=5)
+                _, d1 = B.spmv_select_runtime(h, 1)
+                _, d1k = B.spmv_select_runtime(h, 1000)
+                gate = {"default_csr_us": round(t_def, 2),
+                        "predicted_default_csr_us": round(d1.predicted_us_current, 2),
+                        "predicted_selected_us": round(d1.predicted_us_selected, 2),
+                        "predicted_convert_ms": round(d1.predicted_pack_us / 1e3, 3),
+                        "measured_select_ms": round(d1.measured_select_us / 1e3, 3),
+                        "convert_at_1_run": int(d1.convert), "convert_at_1000_runs": int(d1k.convert)}
             t0 = time.perf_counter()
             sel_cfg, _ = B.spmv_select(h)
             t_select = time.perf_counter() - t0
@@ -400,17 +530,19 @@ def ours(args, world, rank, local):
             chosen = {kk: getattr(sel_cfg, kk) for kk, _ in sel_cfg._fields_}
             source = "selector"
             selector_rows.append({"matrix": mname, "selected": fmt_name(chosen), "selected_us": round(t_sel, 2),
-                                  "best": fmt_name(best_cfg), "best_us": round(best_t, 2),
-                                  "slowdown": round(t_sel / best_t, 4),
+                                  "best": fmt_name(best_cfg) if best_cfg else None,
+                                  "best_us": round(best_t, 2) if best_t else None,
+                                  "slowdown": round(t_sel / best_t, 4) if best_t else None,
                                   "overhead_ms": {"coo_to_csr": round(t_create * 1e3, 2),
                                                   "features": round(t_feat * 1e3, 3),
                                                   "select": round(t_select * 1e3, 3),
-                                                  "pack_selected": round(t_pack * 1e3, 2)}})
+                                                  "pack_selected": round(t_pack * 1e3, 2)},
+                                  "runtime_gate": gate})
         else:
             B.spmv_set_config(h, B.make_config(**best_cfg))
         info = B.spmv_get_info(h)
         mats.append({"matrix": mname, "h": h, "x": x, "y": y, "nnz": nnz, "bytes": nbytes, "cfg": chosen,
-                     "source": source, "best_us": best_t,
+                     "source": source, "best_us": best_t, "per_fmt": per_fmt,
                      "launches": (2 if info.format == B.FMT_HYB and info.hyb_coo_nnz > 0 else 1)})
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
@@ -459,11 +591,29 @@ def ours(args, world, rank, local):
     h2d = sum(t.numel() * t.element_size() for t in xs_host)
     d2h = sum(t.numel() * t.element_size() for t in ys_host)
 
+    # copies overlap the products: x of matrix i+1 goes up and y of matrix
+    # i-1 comes down while matrix i multiplies.  Per matrix, the upload waits
+    # for the previous step's product (it overwrites x), the product for its
+    # upload and for the previous step's download of y (it overwrites y).
+    up, down = torch.cuda.Stream(), torch.cuda.Stream()
+    ev = lambda: torch.cuda.Event()
+    in_done, k_done, out_done = ([ev() for _ in mats] for _ in range(3))
+
     def e2e_step():
         for i, p in enumerate(mats):
-            p["x"].copy_(xs_host[i], non_blocking=True)
+            up.wait_event(k_done[i])
+            with torch.cuda.stream(up):
+                p["x"].copy_(xs_host[i], non_blocking=True)
+            in_done[i].record(up)
+        for i, p in enumerate(mats):
+            stream.wait_event(in_done[i])
+            stream.wait_event(out_done[i])
             B.spmv_run(p["h"], 1.0, p["x"], 0.0, p["y"], sh)
-            ys_host[i].copy_(p["y"], non_blocking=True)
+            k_done[i].record(stream)
+            down.wait_event(k_done[i])
+            with torch.cuda.stream(down):
+                ys_host[i].copy_(p["y"], non_blocking=True)
+            out_done[i].record(down)
 
     e2e_step()
     torch.cuda.synchronize()
@@ -472,11 +622,17 @@ def ours(args, world, rank, local):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
+    up.wait_event(e0)
     for _ in range(args.e2e_steps):
         e2e_step()
+    for d in out_done:
+        stream.wait_event(d)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
+    for i, p in enumerate(mats):        # the downloaded results are the products
+        if not torch.equal(ys_host[i], p["y"].cpu()):
+            raise SystemExit(f"e2e: downloaded y of {p['matrix']} differs from the device result")
     e2e_ms = replicas.max_over_ranks(e2e_ms, device="cuda")
     e2e_value = replicas.whole_job_rate(flops_step, args.e2e_steps, world, e2e_ms) / 1e9
 
@@ -502,9 +658,14 @@ def ours(args, world, rank, local):
         fs["frac"] = round(fs["gbs"] / peak, 4)
         fs["format_frac"] = round(fs["format_gbs"] / peak, 4)
     clocks = clk.summary()
-    batched = None
+    batched = cg = None
     if not args.no_batched and only is None and not args.fixed:
         batched = batched_section(B, matgen, torch)
+    energy_rep = None
+    if not args.no_energy and not args.fixed:
+        energy_rep = energy_section(B, torch, mats, gpu_index)
+    if not args.no_cg and only is None and not args.fixed and args.scale == "full" and vt == B.SPMV_F64:
+        cg = cg_section(B, matgen, torch, S, have_v2)
     if rank != 0:
         for p in mats:
             B.spmv_destroy(p["h"])
@@ -514,7 +675,7 @@ def ours(args, world, rank, local):
     cfg["parallelism"] = f"replicas{world}" if world > 1 else "single"
     cfg["matrices"] = {p["matrix"]: p["nnz"] for p in mats}
     sel_summary = None
-    if selector_rows:
+    if selector_rows and all(r["slowdown"] for r in selector_rows):
         sl = np.array([r["slowdown"] for r in selector_rows])
         sel_summary = {"per_matrix": selector_rows, "geomean_slowdown": round(float(np.exp(np.mean(np.log(sl)))), 4),
                        "within_10pct": float(np.mean(sl <= 1.10))}
@@ -527,7 +688,7 @@ def ours(args, world, rank, local):
                     "d2h_bytes_per_step": d2h},
             "clocks": clocks, "gpu_launches": sum(p["launches"] for p in mats) * args.steps,
             "per_kernel": per_kernel, "selector": sel_summary, "format_sweep": format_sweep,
-            "batched": batched}
+            "batched": batched, "cg": cg, "energy": energy_rep}
     print(json.dumps(line), flush=True)
     for p in mats:
         B.spmv_destroy(p["h"])

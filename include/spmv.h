@@ -84,11 +84,13 @@ typedef enum {
  *                     SELL (one lane per row).
  *   unroll            1, 2 or 4 (8 also for ELL, HYB and SELL): loads in
  *                     flight per lane (ELL, SELL, CSR) or items per lane / 4
- *                     (COO, HYB tail, split CSR; at most 16 items); default
- *                     4 for ELL, HYB and SELL, 2 otherwise.
- *   regcap            register cap per thread: 64 (default; the ceiling
- *                     that keeps 1024-thread blocks launchable) or 32
- *                     (the paper's maxrregcount knob).
+ *                     (COO, HYB tail, split CSR; at most 16 items).  0 =
+ *                     default: ELL and HYB 2 with fp64 values, 4 with
+ *                     fp32/bf16; SELL 8; every other format 2.
+ *   regcap            register cap per thread, 32 (the paper's
+ *                     maxrregcount knob) or 64 (the ceiling that keeps
+ *                     1024-thread blocks launchable).  0 = default: 32 for
+ *                     ELL and HYB, 64 otherwise.
  *   carveout          preferred shared-memory carveout in percent (0..100),
  *                     or -1 to leave the driver default (Section 4 item 3).
  *                     Zero means 0 % (maximum L1), not "default".
@@ -96,7 +98,9 @@ typedef enum {
  *   hyb_ell_width     HYB ELL width; 0 applies the width rule (the largest
  *                     k such that at least max(4096, m/3) rows hold k or
  *                     more nonzeros).
- * spmv_config_default() fills the defaults (with carveout = -1).
+ * spmv_config_default() fills the defaults (carveout = -1; unroll and
+ * regcap 0, resolved per format and value type when the configuration is
+ * applied; spmv_get_config returns the resolved values).
  */
 typedef struct {
     int32_t format;
@@ -123,7 +127,8 @@ typedef struct {
     int32_t format;       /* active spmv_format                            */
 } spmv_info;
 
-/* Fills *cfg with the library defaults for `format` (carveout = -1). */
+/* Fills *cfg with the library defaults for `format` (carveout = -1; unroll
+ * and regcap 0, resolved when the configuration is applied). */
 SPMV_API void spmv_config_default(spmv_config *cfg, int32_t format);
 
 /*

@@ -87,21 +87,29 @@ bool pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1))
 // Loads in flight per thread: ELL (and the ELL part of HYB) keeps four
 // column/value pairs in flight (measured fastest on regular matrices), the
 // other kernels two (or 8 entries per lane for the chunked kernels).
-int default_unroll(int format) {
-    return format == SPMV_FMT_ELL || format == SPMV_FMT_HYB || format == SPMV_FMT_SELL ? 4 : 2;
+// Loads in flight per lane when the configuration leaves unroll at 0.  ELL
+// and HYB with fp64 values keep two (a group of four fp64 loads needs more
+// registers than the 32-register variant has, and the loads then wait on
+// each other); fp32/bf16 keep four; SELL keeps eight with 64 registers.
+int default_unroll(int format, int vt) {
+    if (format == SPMV_FMT_SELL) return 8;
+    if (format == SPMV_FMT_ELL || format == SPMV_FMT_HYB) return vt == SPMV_F64 ? 2 : 4;
+    return 2;
 }
+
+// Register cap when the configuration leaves regcap at 0: ELL and HYB run
+// the 32-register variant (two 1024-thread blocks per SM), the rest 64.
+int default_regcap(int format) { return format == SPMV_FMT_ELL || format == SPMV_FMT_HYB ? 32 : 64; }
 
 // Fills defaults and validates; returns SPMV_ERR_INVALID on a bad field.
 int resolve_config(const spmv_matrix *h, const spmv_config *in, spmv_config *out) {
     spmv_config c;
     spmv_config_default(&c, SPMV_FMT_CSR);
-    if (in) {
-        c = *in;
-        if (c.threads_per_block == 0) c.threads_per_block = 256;
-        if (c.unroll == 0) c.unroll = default_unroll(c.format);
-        if (c.regcap == 0) c.regcap = 64;
-        if (c.bsr_block == 0) c.bsr_block = 4;
-    }
+    if (in) c = *in;
+    if (c.threads_per_block == 0) c.threads_per_block = 256;
+    if (c.unroll == 0) c.unroll = default_unroll(c.format, h->vt);
+    if (c.regcap == 0) c.regcap = default_regcap(c.format);
+    if (c.bsr_block == 0) c.bsr_block = 4;
     if (c.format < SPMV_FMT_CSR || c.format > SPMV_FMT_SELL) {
         set_error("config: unknown format %d", c.format);
         return SPMV_ERR_INVALID;
@@ -205,8 +213,8 @@ void spmv_config_default(spmv_config *cfg, int32_t format) {
     cfg->format = format;
     cfg->threads_per_block = 256;
     cfg->threads_per_row = 0;
-    cfg->unroll = default_unroll(format);
-    cfg->regcap = 64;
+    cfg->unroll = 0;  // per format and value type, resolved when applied
+    cfg->regcap = 0;
     cfg->carveout = -1;
     cfg->bsr_block = 4;
     cfg->hyb_ell_width = 0;

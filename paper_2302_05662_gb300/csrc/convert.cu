@@ -424,18 +424,18 @@ __global__ void k_tail_counts(const int *rowptr, int64_t m, int width, int *cnt)
         cnt[r] = max(0, rowptr[r + 1] - rowptr[r] - width);
 }
 
+// tail entry o belongs to the row r with tptr[r] <= o < tptr[r+1]; entries
+// are spread over the threads (long rows do not serialise on one thread)
 template <typename V>
 __global__ void k_hyb_tail(const int *rowptr, const int *colidx, const V *vals, int64_t m, int width,
-                           const int *tptr, int *trows, int *tcols, V *tvals) {
+                           const int *tptr, int64_t tail, int *trows, int *tcols, V *tvals) {
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < m; r += stride) {
-        int s = rowptr[r] + width, e = rowptr[r + 1];
-        int o = tptr[r];
-        for (int k = s; k < e; ++k, ++o) {
-            trows[o] = (int)r;
-            tcols[o] = colidx[k];
-            tvals[o] = vals[k];
-        }
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < tail; o += stride) {
+        const int r = row_of(tptr, m, o);
+        const int64_t k = (int64_t)rowptr[r] + width + (o - tptr[r]);
+        trows[o] = r;
+        tcols[o] = colidx[k];
+        tvals[o] = vals[k];
     }
 }
 
@@ -541,26 +541,35 @@ __global__ void k_sell_widths(const int *rowptr, const uint32_t *perm, int64_t m
     }
 }
 
+// one warp per 32-slot column (slice sl, entry k) of the layout: slots of a
+// slice come in multiples of 32, so the warp finds (sl, k) with one binary
+// search (same address in every lane) and lane l fills sorted row 32 sl + l
 template <typename V>
 __global__ void k_sell_fill(const int *rowptr, const int *colidx, const V *vals, const uint32_t *perm, int64_t m,
-                            int64_t nslices, const int *sptr, int *scol, V *sval, int *sperm) {
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nslices * 32; p += stride) {
-        const int64_t sl = p / 32, lane = p % 32;
-        const int64_t base = sptr[sl], width = (sptr[sl + 1] - base) / 32;
-        int64_t rs = 0, len = 0;
-        if (p < m) {
-            const uint32_t r = perm[p];
-            sperm[p] = (int)r;
-            rs = rowptr[r];
-            len = rowptr[r + 1] - rs;
+                            int64_t nslices, const int *sptr, int64_t total, int *scol, V *sval, int *sperm) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w = warp; w < total / 32; w += nwarps) {
+        const int64_t p0 = 32 * w;
+        const int sl = row_of(sptr, nslices, p0);
+        const int64_t k = (p0 - sptr[sl]) / 32;
+        const int64_t q = (int64_t)sl * 32 + lane;
+        int c = -1;
+        V v = V(0.0f);
+        if (q < m) {
+            const uint32_t r = perm[q];
+            const int64_t rs = rowptr[r];
+            if (k < rowptr[r + 1] - rs) {
+                c = colidx[rs + k];
+                v = vals[rs + k];
+            }
         }
-        for (int64_t k = 0; k < width; ++k) {
-            const bool have = k < len;
-            scol[base + 32 * k + lane] = have ? colidx[rs + k] : -1;
-            sval[base + 32 * k + lane] = have ? vals[rs + k] : V(0.0f);
-        }
+        scol[p0 + lane] = c;
+        sval[p0 + lane] = v;
     }
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < m; q += stride) sperm[q] = (int)perm[q];
 }
 
 // work items per slice: ceil(width / kmax), at least one
@@ -833,16 +842,16 @@ int pack_hyb(spmv_matrix *h, int64_t width, cudaStream_t s) {
     SPMV_TRY(dalloc(&h->hyb_cols, (size_t)tail));
     SPMV_TRY(dalloc_bytes(&h->hyb_vals, vs * tail));
     if (tail > 0) {
-        unsigned g = grid1d(m, 256);
+        unsigned g = grid1d(tail, 256);
         if (h->vt == SPMV_F64)
             k_hyb_tail<double><<<g, 256, 0, s>>>(h->rowptr, h->colidx, (const double *)h->vals, m, (int)width,
-                                                 h->hyb_ptr, h->hyb_rows, h->hyb_cols, (double *)h->hyb_vals);
+                                                 h->hyb_ptr, tail, h->hyb_rows, h->hyb_cols, (double *)h->hyb_vals);
         else if (h->vt == SPMV_F32)
             k_hyb_tail<float><<<g, 256, 0, s>>>(h->rowptr, h->colidx, (const float *)h->vals, m, (int)width,
-                                                h->hyb_ptr, h->hyb_rows, h->hyb_cols, (float *)h->hyb_vals);
+                                                h->hyb_ptr, tail, h->hyb_rows, h->hyb_cols, (float *)h->hyb_vals);
         else
             k_hyb_tail<__nv_bfloat16><<<g, 256, 0, s>>>(h->rowptr, h->colidx, (const __nv_bfloat16 *)h->vals, m,
-                                                        (int)width, h->hyb_ptr, h->hyb_rows, h->hyb_cols,
+                                                        (int)width, h->hyb_ptr, tail, h->hyb_rows, h->hyb_cols,
                                                         (__nv_bfloat16 *)h->hyb_vals);
         SPMV_CUDA_TRY(cudaGetLastError());
     }
@@ -948,23 +957,23 @@ int pack_sell(spmv_matrix *h, cudaStream_t s) {
     k_sell_widths<<<grid1d(nslices, 256), 256, 0, s>>>(h->rowptr, perm, m, nslices, slots.p);
     int64_t total = 0;
     SPMV_TRY(exclusive_scan(slots.p, h->sell_ptr, nslices + 1, s, &total));
-    if ((double)total > 8.0 * (double)h->nnz + (double)(1 << 24)) {
-        set_error("SELL: %lld padded slots exceed 8 x nnz + 2^24", (long long)total);
+    if ((double)total > 8.0 * (double)h->nnz + (double)(1 << 24) || total >= (int64_t(1) << 31)) {
+        set_error("SELL: %lld padded slots exceed min(8 x nnz + 2^24, 2^31 - 1)", (long long)total);
         return SPMV_ERR_UNSUPPORTED;
     }
     h->sell_slots = total;
     SPMV_TRY(dalloc(&h->sell_col, (size_t)total));
     SPMV_TRY(dalloc_bytes(&h->sell_val, vs * total));
-    const unsigned g = grid1d(nslices * 32, 256);
+    const unsigned g = grid1d(std::max<int64_t>(total, m), 256);
     if (h->vt == SPMV_F64)
         k_sell_fill<double><<<g, 256, 0, s>>>(h->rowptr, h->colidx, (const double *)h->vals, perm, m, nslices,
-                                              h->sell_ptr, h->sell_col, (double *)h->sell_val, h->sell_perm);
+                                              h->sell_ptr, total, h->sell_col, (double *)h->sell_val, h->sell_perm);
     else if (h->vt == SPMV_F32)
         k_sell_fill<float><<<g, 256, 0, s>>>(h->rowptr, h->colidx, (const float *)h->vals, perm, m, nslices,
-                                             h->sell_ptr, h->sell_col, (float *)h->sell_val, h->sell_perm);
+                                             h->sell_ptr, total, h->sell_col, (float *)h->sell_val, h->sell_perm);
     else
         k_sell_fill<__nv_bfloat16><<<g, 256, 0, s>>>(h->rowptr, h->colidx, (const __nv_bfloat16 *)h->vals, perm, m,
-                                                     nslices, h->sell_ptr, h->sell_col,
+                                                     nslices, h->sell_ptr, total, h->sell_col,
                                                      (__nv_bfloat16 *)h->sell_val, h->sell_perm);
     SPMV_CUDA_TRY(cudaGetLastError());
     // work items (slice, k range) and the partials joining a slice's items

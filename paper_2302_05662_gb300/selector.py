@@ -25,8 +25,12 @@ from . import binding as B
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_BLOB = os.path.join(PKG, "selector_gb300.f32")
-# the exhaustive-sweep records the committed selector was trained on
+# the exhaustive-sweep records the committed selector was trained on: the
+# full sweep, a supplementary SELL sweep of the same 2000 matrices, and the
+# conversion-time calibration of its cost model
 DEFAULT_DATA = os.path.join(PKG, "data", "sweep_gb300_f64.jsonl.gz")
+DEFAULT_SUPPLEMENT = os.path.join(PKG, "data", "sweep_gb300_f64_sell.jsonl.gz")
+DEFAULT_CALIB = os.path.join(PKG, "data", "convert_calib_gb300_f64.jsonl.gz")
 MAGIC, VERSION = 2302.0, 1.0
 CFG_FIELDS = ("format", "threads_per_block", "threads_per_row", "unroll", "regcap", "carveout",
               "bsr_block", "hyb_ell_width")
@@ -98,13 +102,24 @@ def load_default_selector(path: str = DEFAULT_BLOB) -> dict:
     return parse_blob(blob)
 
 
+def default_is_v2(path: str = DEFAULT_BLOB) -> bool:
+    """Whether the committed blob carries the time head and conversion model."""
+    import os
+    return os.path.exists(path) and parse_blob(np.fromfile(path, dtype=np.float32))["version"] >= 2
+
+
 # ---------------------------------------------------------------------------
 # dataset from sweep records
 # ---------------------------------------------------------------------------
 def load_records(paths):
-    """Sweep records (JSON lines, optionally gzip-compressed) keyed by matrix."""
+    """Sweep records (JSON lines, optionally gzip-compressed) keyed by matrix.
+
+    Supplementary records (a later sweep of some formats only) are merged
+    into the full record of the same matrix: their times are rescaled by the
+    ratio of the two default-CSR times measured in each sweep, so that
+    timings taken on another GPU or day land on the full record's scale."""
     import gzip
-    recs = {}
+    recs, supp = {}, []
     for p in paths:
         with (gzip.open(p, "rt") if p.endswith(".gz") else open(p)) as fh:
             for line in fh:
@@ -114,7 +129,23 @@ def load_records(paths):
                     continue
                 if "features" in r:
                     recs[r["matrix"]] = r
+                elif "supplement" in r:
+                    supp.append(r)
+    for r in supp:
+        base = recs.get(r["matrix"])
+        if base is None or not base.get("default_us") or not r.get("default_us"):
+            continue
+        scale = base["default_us"] / r["default_us"]
+        tm = dict((k, t) for k, t in base["times"])
+        for k, t in r["times"]:
+            tm[k] = None if t is None else t * scale
+        base["times"] = [[k, t] for k, t in tm.items()]
     return [recs[k] for k in sorted(recs)]
+
+
+def has_sell(records) -> bool:
+    """Whether any record holds SELL timings (then SELL joins the labels)."""
+    return any(k.startswith("format=5,") for r in records for k, _ in r["times"])
 
 
 def dataset(records, label_keys):
@@ -273,7 +304,7 @@ def main():
     ap.add_argument("--calib", nargs="*", default=None, help="conversion-time records (JSON lines)")
     args = ap.parse_args()
     recs = load_records(args.data)
-    labels = sweep.label_space()
+    labels = sweep.label_space(include_sell=has_sell(recs))
     keys = [sweep.config_key(c) for c in labels]
     X, T, D, ids, fams = dataset(recs, keys)
     ok = np.isfinite(T).any(axis=1) & np.isfinite(D)

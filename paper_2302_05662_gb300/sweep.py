@@ -33,9 +33,9 @@ CSR_TPR = (1, 2, 4, 8, 16, 32, B.TPR_SPLIT)
 
 def label_space(tpb=TPB, include_sell: bool = False):
     """The selector's label space: (format, threads_per_block, threads_per_row)
-    points, each a dict of spmv_config fields.  The committed selector was
-    trained without SELL (include_sell=False); the benchmark's exhaustive
-    search includes it."""
+    points, each a dict of spmv_config fields.  include_sell adds the six
+    SELL points (the committed selector's 78 classes include them; its SELL
+    timings come from a supplementary sweep)."""
     out = []
     if include_sell:
         out += [dict(format=B.FMT_SELL, threads_per_block=t) for t in tpb]
@@ -53,8 +53,9 @@ def label_space(tpb=TPB, include_sell: bool = False):
 def refine_space(best: dict):
     """Register cap x unroll x carveout around a winning point."""
     out = []
+    ell_family = best.get("format", 0) in (B.FMT_ELL, B.FMT_HYB, B.FMT_SELL)
     for rc in (32, 64):
-        for u in (1, 2, 4):
+        for u in ((1, 2, 4, 8) if ell_family else (1, 2, 4)):
             for cv in (-1, 0, 100):
                 d = dict(best)
                 d.update(regcap=rc, unroll=u, carveout=cv)
@@ -120,7 +121,7 @@ def sweep_matrix(coo, space, timer: Timer, reps=7, value_dtype="f64", seed=0):
     # launch parameters alone reuses the packed arrays
     def pack_key(i):
         c = space[i]
-        return (c.get("format", 0), c.get("threads_per_row", 0), c.get("bsr_block", 4), c.get("unroll", 2),
+        return (c.get("format", 0), c.get("threads_per_row", 0), c.get("bsr_block", 4), c.get("unroll", 0),
                 c.get("hyb_ell_width", 0))
     refused = set()
     try:
@@ -214,6 +215,9 @@ def main():
     ap.add_argument("--time-budget", type=float, default=1e9, help="seconds; stop cleanly after")
     ap.add_argument("--calibrate-pack", action="store_true",
                     help="time format conversions of matrices start..start+count instead")
+    ap.add_argument("--formats", default=None,
+                    help="comma list (csr,ell,coo,hyb,bsr,sell): a supplementary sweep of these formats' "
+                         "label points only, merged into earlier records by the selector trainer")
     args = ap.parse_args()
     from . import build
     build.build()
@@ -230,7 +234,12 @@ def main():
                 except Exception:
                     pass
     timer = Timer()
-    space = label_space()
+    space = label_space(include_sell=args.formats is not None)
+    if args.formats is not None:
+        names = {"csr": B.FMT_CSR, "ell": B.FMT_ELL, "coo": B.FMT_COO, "hyb": B.FMT_HYB, "bsr": B.FMT_BSR,
+                 "sell": B.FMT_SELL}
+        keep = {names[f] for f in args.formats.split(",")}
+        space = [c for c in space if c["format"] in keep]
     t0 = time.time()
     with open(args.out, "a") as fh:
         for idx in range(args.start, args.start + args.count):
@@ -240,10 +249,12 @@ def main():
                 break
             fam, coo = generate_dataset_matrix(idx, n_hi=args.n_hi)
             res = sweep_matrix(coo, space + [default_csr(coo)], timer, reps=args.reps, seed=idx)
-            feats = matrix_features(coo)
             rec = {"matrix": idx, "family": fam, "m": coo.m, "n": coo.n, "nnz": coo.nnz,
-                   "features": [float(v) for v in feats], "default_us": res[-1][1],
-                   "times": [[config_key(c), t] for c, t in res[:-1]]}
+                   "default_us": res[-1][1], "times": [[config_key(c), t] for c, t in res[:-1]]}
+            if args.formats is None:
+                rec["features"] = [float(v) for v in matrix_features(coo)]
+            else:
+                rec["supplement"] = args.formats
             fh.write(json.dumps(rec) + "\n")
             fh.flush()
 

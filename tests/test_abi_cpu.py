@@ -51,10 +51,10 @@ def test_only_the_abi_is_exported(lib):
 def test_config_default_host_only(lib):
     cfg = binding.spmv_config()
     lib.spmv_config_default(ctypes.byref(cfg), binding.FMT_BSR)
-    assert cfg.as_dict() == {"format": 4, "threads_per_block": 256, "threads_per_row": 0, "unroll": 2,
-                             "regcap": 64, "carveout": -1, "bsr_block": 4, "hyb_ell_width": 0}
+    assert cfg.as_dict() == {"format": 4, "threads_per_block": 256, "threads_per_row": 0, "unroll": 0,
+                             "regcap": 0, "carveout": -1, "bsr_block": 4, "hyb_ell_width": 0}
     lib.spmv_config_default(ctypes.byref(cfg), binding.FMT_ELL)
-    assert cfg.unroll == 4
+    assert cfg.format == binding.FMT_ELL and cfg.unroll == 0 and cfg.regcap == 0
 
 
 def test_host_argument_errors(lib):

@@ -56,8 +56,13 @@ def test_committed_selector_matches_its_report():
         import pytest
         pytest.skip("no committed selector")
     p = S.parse_blob(np.fromfile(S.DEFAULT_BLOB, dtype=np.float32))
-    recs = S.load_records([S.DEFAULT_DATA])
-    keys = [sweep.config_key(c) for c in sweep.label_space()]
+    recs = S.load_records([S.DEFAULT_DATA, S.DEFAULT_SUPPLEMENT])
+    labels = sweep.label_space(include_sell=S.has_sell(recs))
+    keys = [sweep.config_key(c) for c in labels]
+    assert len(labels) == p["K"] == 78
+    for k, c in enumerate(labels):                   # the blob's classes are the label space, in order
+        lab = dict(zip(S.CFG_FIELDS, p["labels"][k].tolist()))
+        assert all(lab[f] == c.get(f, 0) for f in ("format", "threads_per_block", "threads_per_row"))
     X, T, D, ids, fams = S.dataset(recs, keys)
     msk = (ids >= 1800) & np.isfinite(T).any(axis=1) & np.isfinite(D)
     w = {k: p[k].astype(np.float64) for k in ("mu", "sigma", "W1", "b1", "W2", "b2")}
@@ -68,6 +73,7 @@ def test_committed_selector_matches_its_report():
     assert abs(got["within_10pct"] - rep["heldout"]["within_10pct"]) <= 0.01
     assert got["within_10pct"] >= 0.90
     assert got["geomean_speedup_vs_default_csr"] > 1.0
+    assert p["version"] == 2 and rep["pack_model_heldout"]["r2"] > 0.9
 
 
 def test_blob_v2_roundtrip_and_heads():
@@ -108,3 +114,23 @@ def test_pack_model_fit_and_gate():
     assert not S.gate_decision(100.0, 60.0, 1000.0, 500.0, 37)
     assert S.gate_decision(100.0, 60.0, 1000.0, 500.0, 38)
     assert not S.gate_decision(50.0, 60.0, 0.0, 0.0, 10 ** 9)      # never when slower
+
+
+def test_supplementary_records_merge_on_the_base_scale(tmp_path):
+    import json
+    base = {"matrix": 3, "family": "stencil", "features": [0.0] * 20, "default_us": 100.0,
+            "times": [["format=0,threads_per_block=32,threads_per_row=1", 50.0],
+                      ["format=1,threads_per_block=32", None]]}
+    supp = {"matrix": 3, "family": "stencil", "default_us": 200.0, "supplement": "sell",
+            "times": [["format=5,threads_per_block=32", 80.0], ["format=5,threads_per_block=64", None]]}
+    orphan = dict(supp, matrix=4)
+    p1, p2 = tmp_path / "a.jsonl", tmp_path / "b.jsonl"
+    p1.write_text(json.dumps(base) + "\n")
+    p2.write_text(json.dumps(supp) + "\n" + json.dumps(orphan) + "\n")
+    recs = S.load_records([str(p1), str(p2)])
+    assert [r["matrix"] for r in recs] == [3]
+    tm = dict((k, t) for k, t in recs[0]["times"])
+    assert tm["format=5,threads_per_block=32"] == 40.0          # 80 us x (100 / 200)
+    assert tm["format=5,threads_per_block=64"] is None
+    assert tm["format=0,threads_per_block=32,threads_per_row=1"] == 50.0
+    assert S.has_sell(recs) and not S.has_sell(S.load_records([str(p1)]))
