@@ -125,6 +125,8 @@ typedef struct {
     int64_t format_bytes; /* device bytes the active format's kernel reads */
     int32_t value_type;   /* spmv_dtype                                    */
     int32_t format;       /* active spmv_format                            */
+    int32_t panels;       /* row panels the matrix is held in (>= 1)       */
+    int32_t reserved;
 } spmv_info;
 
 /* Fills *cfg with the library defaults for `format` (carveout = -1; unroll
@@ -143,7 +145,7 @@ SPMV_API void spmv_config_default(spmv_config *cfg, int32_t format);
  * active format and kernel.  m, n may be 0; nnz may be 0.
  * Errors: SPMV_ERR_INVALID for negative sizes, a NULL array with nnz > 0,
  * or any triplet outside [0,m) x [0,n) (checked on the device);
- * SPMV_ERR_UNSUPPORTED for m, n or nnz >= 2^31 or a format whose padded
+ * SPMV_ERR_UNSUPPORTED for m or n >= 2^31 or a format whose padded
  * storage exceeds 8 nnz + 2^24 value slots (ELL width x rows; BSR blocks x
  * r^2; SELL slices x 32 x slice width); SPMV_ERR_OOM; SPMV_ERR_CUDA.
  * Synchronises `stream`.
@@ -431,6 +433,26 @@ typedef struct {
 SPMV_API int spmv_cg(spmv_handle h, const void *d_b, void *d_x, double tol,
                      int32_t maxit, double *d_rho, spmv_cg_result *out,
                      void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Row panels.  One handle indexes its nonzeros with int32 offsets, so a
+ * matrix given with more triplets than the panel limit is held as several
+ * sub-handles over contiguous row ranges (boundaries at multiples of 4 rows,
+ * each range with at most `limit` triplets); spmv_run, spmv_set_config,
+ * spmv_features, spmv_select(_runtime) and spmv_cg treat it as one matrix
+ * (features and results as for a single handle; each panel runs its own
+ * kernels on its rows of y).  spmv_export and spmv_batch_create refuse a
+ * panelled handle (SPMV_ERR_UNSUPPORTED), and so does spmv_create when four
+ * consecutive rows alone hold more than `limit` triplets.  The default and
+ * largest limit, SPMV_PANEL_LIMIT_MAX = 2^31 - 2^20, keeps every offset and
+ * loop counter of a panel's kernels inside int32 with headroom; a smaller
+ * limit (process-wide, for handles created afterwards) exercises panels on
+ * small matrices or bounds the conversion scratch.
+ * Errors: SPMV_ERR_INVALID for a limit outside [1, SPMV_PANEL_LIMIT_MAX].
+ * ------------------------------------------------------------------------- */
+#define SPMV_PANEL_LIMIT_MAX 2146435072LL
+SPMV_API int spmv_set_panel_limit(int64_t max_triplets);
+SPMV_API int64_t spmv_get_panel_limit(void);
 
 /* Frees every device array of the handle.  NULL is accepted. */
 SPMV_API int spmv_destroy(spmv_handle h);

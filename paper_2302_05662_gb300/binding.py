@@ -31,7 +31,7 @@ EXPORTED = ("spmv_config_default", "spmv_create", "spmv_set_config", "spmv_get_c
             "spmv_last_error", "spmv_coo_run_noalloc", "spmv_features", "spmv_selector_load",
             "spmv_selector_infer", "spmv_select", "spmv_batch_create", "spmv_batch_tune",
             "spmv_batch_launch", "spmv_batch_get_plan", "spmv_batch_destroy", "spmv_batch_run",
-            "spmv_select_runtime", "spmv_cg")
+            "spmv_select_runtime", "spmv_cg", "spmv_set_panel_limit", "spmv_get_panel_limit")
 
 
 class SpmvError(RuntimeError):
@@ -77,7 +77,7 @@ class spmv_info(ctypes.Structure):
                 ("max_row", ctypes.c_int64), ("ell_width", ctypes.c_int64),
                 ("hyb_coo_nnz", ctypes.c_int64), ("bsr_blocks", ctypes.c_int64), ("sell_slots", ctypes.c_int64),
                 ("format_bytes", ctypes.c_int64), ("value_type", ctypes.c_int32),
-                ("format", ctypes.c_int32)]
+                ("format", ctypes.c_int32), ("panels", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -126,6 +126,8 @@ def load_library(path: str | None = None):
         "spmv_coo_run_noalloc": (ctypes.c_int, [_I64, _I64, _I64, _VP, _VP, _VP, _I32, _D, _VP, _D, _VP,
                                                 _VP]),
         "spmv_cg": (ctypes.c_int, [_VP, _VP, _VP, _D, _I32, _VP, ctypes.POINTER(spmv_cg_result), _VP]),
+        "spmv_set_panel_limit": (ctypes.c_int, [_I64]),
+        "spmv_get_panel_limit": (_I64, []),
         "spmv_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -324,6 +326,16 @@ def spmv_cg(h: int, b, x, tol: float, maxit: int, rho=None, stream=None) -> spmv
     return out
 
 
+def spmv_set_panel_limit(max_triplets: int):
+    """Triplet count above which spmv_create holds a matrix in row panels."""
+    _check(load_library().spmv_set_panel_limit(int(max_triplets)))
+
+
+def spmv_get_panel_limit() -> int:
+    return int(load_library().spmv_get_panel_limit())
+
+
+PANEL_LIMIT_DEFAULT = (1 << 31) - (1 << 20)
 NOALLOC_MAX_NNZ = 1 << 25
 
 

@@ -1,6 +1,7 @@
 // C ABI of the SpMV engine (include/spmv.h): handle life cycle, format
 // selection, and dispatch of y = alpha*A*x + beta*y to the kernel families.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -176,6 +177,16 @@ int runner(const spmv_matrix *h, int kind, double alpha, const void *x, double b
 
 void destroy_all(spmv_matrix *h) {
     free_cg(h);
+    for (int p = 0; p < h->npanels; ++p)
+        if (h->panels[p]) {
+            destroy_all(h->panels[p]);
+            delete h->panels[p];
+        }
+    delete[] h->panels;
+    delete[] h->panel_row0;
+    h->panels = nullptr;
+    h->panel_row0 = nullptr;
+    h->npanels = 0;
     free_packed(h);
     if (h->rowptr) cudaFree(h->rowptr);
     if (h->colidx) cudaFree(h->colidx);
@@ -187,6 +198,12 @@ void destroy_all(spmv_matrix *h) {
 }  // namespace
 
 int run_product(const spmv_matrix *h, double alpha, const void *x, double beta, void *y, cudaStream_t s) {
+    if (h->npanels > 0) {  // each panel writes its own rows of y
+        for (int p = 0; p < h->npanels; ++p)
+            SPMV_TRY(run_product(h->panels[p], alpha, x, beta,
+                                 static_cast<char *>(y) + vec_size(h->vt) * (size_t)h->panel_row0[p], s));
+        return SPMV_OK;
+    }
     if (h->nnz == 0) return runner(h, RUN_SCALE, alpha, x, beta, y, s);
     switch (h->cfg.format) {
     case SPMV_FMT_CSR:
@@ -201,6 +218,67 @@ int run_product(const spmv_matrix *h, double alpha, const void *x, double beta, 
     set_error("spmv_run: bad format");
     return SPMV_ERR_INVALID;
 }
+
+namespace {
+std::atomic<int64_t> g_panel_limit{SPMV_PANEL_LIMIT_MAX};
+
+// a handle over row panels: sub-handles built from the stably gathered
+// triplets of each panel's rows, so duplicates still sum in triplet order
+int create_panelled(spmv_handle *out, int64_t m, int64_t n, int64_t nnz, const int32_t *d_rows,
+                    const int32_t *d_cols, const void *d_vals, int32_t vt, const spmv_config *cfg,
+                    cudaStream_t s, int64_t limit) {
+    SPMV_TRY(check_triplet_bounds(d_rows, d_cols, nnz, m, n, s));
+    std::vector<int64_t> bounds;
+    SPMV_TRY(plan_panels(d_rows, nnz, m, limit, s, &bounds));
+    spmv_matrix *h = new (std::nothrow) spmv_matrix();
+    if (!h) {
+        set_error("spmv_create: host allocation failed");
+        return SPMV_ERR_OOM;
+    }
+    const int np = (int)bounds.size() - 1;
+    h->m = m;
+    h->n = n;
+    h->vt = vt;
+    h->panels = new (std::nothrow) spmv_matrix *[np]();
+    h->panel_row0 = new (std::nothrow) int64_t[np + 1];
+    if (!h->panels || !h->panel_row0) {
+        delete[] h->panels;
+        delete[] h->panel_row0;
+        delete h;
+        set_error("spmv_create: host allocation failed");
+        return SPMV_ERR_OOM;
+    }
+    h->npanels = np;
+    for (int p = 0; p <= np; ++p) h->panel_row0[p] = bounds[p];
+    int st = SPMV_OK;
+    for (int p = 0; p < np && st == SPMV_OK; ++p) {
+        int32_t *pr = nullptr, *pc = nullptr;
+        void *pv = nullptr;
+        int64_t cnt = 0;
+        st = gather_panel(d_rows, d_cols, d_vals, value_size(vt), nnz, bounds[p], bounds[p + 1], &pr, &pc, &pv,
+                          &cnt, s);
+        if (st == SPMV_OK)
+            st = spmv_create(&h->panels[p], bounds[p + 1] - bounds[p], n, cnt, pr, pc, pv, vt, cfg, (void *)s);
+        cudaFree(pr);
+        cudaFree(pc);
+        cudaFree(pv);
+        if (st == SPMV_OK) {
+            h->nnz += h->panels[p]->nnz;
+            h->max_row = std::max(h->max_row, h->panels[p]->max_row);
+            h->sm_count = h->panels[p]->sm_count;
+        }
+    }
+    if (st != SPMV_OK) {
+        destroy_all(h);
+        delete h;
+        return st;
+    }
+    h->cfg = h->panels[0]->cfg;
+    h->packed = true;
+    *out = h;
+    return SPMV_OK;
+}
+}  // namespace
 
 }  // namespace spmv
 
@@ -222,6 +300,17 @@ void spmv_config_default(spmv_config *cfg, int32_t format) {
 
 const char *spmv_last_error(void) { return g_err; }
 
+int spmv_set_panel_limit(int64_t max_triplets) {
+    if (max_triplets < 1 || max_triplets > SPMV_PANEL_LIMIT_MAX) {
+        set_error("spmv_set_panel_limit: %lld not in [1, 2^31 - 2^20]", (long long)max_triplets);
+        return SPMV_ERR_INVALID;
+    }
+    g_panel_limit.store(max_triplets);
+    return SPMV_OK;
+}
+
+int64_t spmv_get_panel_limit(void) { return g_panel_limit.load(); }
+
 int spmv_create(spmv_handle *out, int64_t m, int64_t n, int64_t nnz, const int32_t *d_rows, const int32_t *d_cols,
                 const void *d_vals, int32_t value_type, const spmv_config *cfg, void *stream) {
     g_err[0] = 0;
@@ -242,8 +331,8 @@ int spmv_create(spmv_handle *out, int64_t m, int64_t n, int64_t nnz, const int32
         set_error("spmv_create: NULL triplet array with nnz > 0");
         return SPMV_ERR_INVALID;
     }
-    if (m >= (int64_t(1) << 31) || n >= (int64_t(1) << 31) || nnz >= (int64_t(1) << 31)) {
-        set_error("spmv_create: m, n and nnz must be below 2^31");
+    if (m >= (int64_t(1) << 31) || n >= (int64_t(1) << 31)) {
+        set_error("spmv_create: m and n must be below 2^31");
         return SPMV_ERR_UNSUPPORTED;
     }
     if (nnz > 0 && (m == 0 || n == 0)) {
@@ -251,6 +340,8 @@ int spmv_create(spmv_handle *out, int64_t m, int64_t n, int64_t nnz, const int32
         return SPMV_ERR_INVALID;
     }
     cudaStream_t s = (cudaStream_t)stream;
+    const int64_t limit = g_panel_limit.load();
+    if (nnz > limit) return create_panelled(out, m, n, nnz, d_rows, d_cols, d_vals, value_type, cfg, s, limit);
     spmv_matrix *h = new (std::nothrow) spmv_matrix();
     if (!h) {
         set_error("spmv_create: host allocation failed");
@@ -289,6 +380,23 @@ int spmv_set_config(spmv_handle h, const spmv_config *cfg, void *stream) {
     }
     spmv_config rc;
     SPMV_TRY(resolve_config(h, cfg, &rc));
+    if (h->npanels > 0) {
+        // every panel takes the configuration, or every panel falls back to CSR
+        free_cg(h);
+        int st = SPMV_OK;
+        for (int p = 0; p < h->npanels && st == SPMV_OK; ++p) st = spmv_set_config(h->panels[p], cfg, stream);
+        if (st != SPMV_OK) {
+            char saved[512];
+            std::strncpy(saved, g_err, sizeof saved);
+            saved[sizeof saved - 1] = 0;
+            spmv_config csr;
+            spmv_config_default(&csr, SPMV_FMT_CSR);
+            for (int p = 0; p < h->npanels; ++p) spmv_set_config(h->panels[p], &csr, stream);
+            std::strncpy(g_err, saved, sizeof g_err);
+        }
+        h->cfg = h->panels[0]->cfg;
+        return st;
+    }
     int st = pack_format(h, rc, (cudaStream_t)stream);
     if (st != SPMV_OK) {
         // leave a usable handle: fall back to plain CSR
@@ -321,12 +429,32 @@ int spmv_get_info(spmv_handle h, spmv_info *out) {
         return SPMV_ERR_INVALID;
     }
     std::memset(out, 0, sizeof *out);
+    if (h->npanels > 0) {  // sums over the panels (widths: the largest)
+        for (int p = 0; p < h->npanels; ++p) {
+            spmv_info pi;
+            SPMV_TRY(spmv_get_info(h->panels[p], &pi));
+            out->ell_width = std::max(out->ell_width, pi.ell_width);
+            out->hyb_coo_nnz += pi.hyb_coo_nnz;
+            out->bsr_blocks += pi.bsr_blocks;
+            out->sell_slots += pi.sell_slots;
+            out->format_bytes += pi.format_bytes;
+        }
+        out->m = h->m;
+        out->n = h->n;
+        out->nnz = h->nnz;
+        out->max_row = h->max_row;
+        out->value_type = h->vt;
+        out->format = h->cfg.format;
+        out->panels = h->npanels;
+        return SPMV_OK;
+    }
     out->m = h->m;
     out->n = h->n;
     out->nnz = h->nnz;
     out->max_row = h->max_row;
     out->value_type = h->vt;
     out->format = h->cfg.format;
+    out->panels = 1;
     const int64_t vs = (int64_t)value_size(h->vt);
     switch (h->cfg.format) {
     case SPMV_FMT_CSR:
@@ -371,6 +499,10 @@ int spmv_run(spmv_handle h, double alpha, const void *d_x, double beta, void *d_
 
 namespace {
 int array_of(spmv_handle h, int32_t id, const void **ptr, int64_t *bytes) {
+    if (h->npanels > 0) {
+        set_error("spmv_export: the matrix is held in %d row panels; arrays are per panel", h->npanels);
+        return SPMV_ERR_UNSUPPORTED;
+    }
     const int64_t vs = (int64_t)value_size(h->vt);
     const bool hyb = h->cfg.format == SPMV_FMT_HYB;
     *ptr = nullptr;

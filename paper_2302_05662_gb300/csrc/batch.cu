@@ -266,6 +266,10 @@ int spmv_batch_create(spmv_batch_handle *out, const spmv_handle *hs, int32_t cou
             return SPMV_ERR_INVALID;
         }
         vt = hs[i]->vt;
+        if (hs[i]->npanels > 0) {
+            set_error("spmv_batch_create: matrix %d is held in row panels (too many nonzeros for a batch)", i);
+            return SPMV_ERR_UNSUPPORTED;
+        }
         if ((hs[i]->m > 0 && !d_y[i]) || (hs[i]->nnz > 0 && !d_x[i])) {
             set_error("spmv_batch_create: NULL vector for matrix %d", i);
             return SPMV_ERR_INVALID;

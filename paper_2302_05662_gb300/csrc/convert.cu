@@ -598,6 +598,98 @@ __global__ void k_sell_item_fill(const int *sptr, int64_t nslices, int kmax, con
     }
 }
 
+// ---------------------------------------------------------------------------
+// row panels: more triplets than one handle indexes with int32 offsets
+// ---------------------------------------------------------------------------
+constexpr int PANEL_CHUNK_SHIFT = 18;  // 2^18-row chunks, a multiple of 4 rows
+constexpr int PC_THREADS = SC_THREADS, PC_ITEMS = 16, PC_TILE = PC_THREADS * PC_ITEMS;
+
+// triplets per 2^18-row chunk; lanes of a warp on the same chunk add once
+__global__ void k_chunk_hist(const int *rows, int64_t nnz, int nchunks, unsigned long long *counts) {
+    extern __shared__ unsigned sh_chunks[];
+    for (int c = threadIdx.x; c < nchunks; c += blockDim.x) sh_chunks[c] = 0;
+    __syncthreads();
+    const unsigned lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t nr = (nnz + 31) / 32 * 32;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += stride) {
+        const int c = i < nnz ? rows[i] >> PANEL_CHUNK_SHIFT : -1;
+        const unsigned peers = __match_any_sync(FULL, c);
+        if (c >= 0 && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(&sh_chunks[c], (unsigned)__popc(peers));
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < nchunks; c += blockDim.x)
+        if (sh_chunks[c]) atomicAdd(&counts[c], (unsigned long long)sh_chunks[c]);
+}
+
+// triplets per 4-row group of rows [lo, hi)
+__global__ void k_group_hist(const int *rows, int64_t nnz, int lo, int hi, unsigned long long *counts) {
+    const unsigned lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t nr = (nnz + 31) / 32 * 32;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += stride) {
+        const int r = i < nnz ? rows[i] : -1;
+        const int g = r >= lo && r < hi ? (r - lo) >> 2 : -1;
+        const unsigned peers = __match_any_sync(FULL, g);
+        if (g >= 0 && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(&counts[g], (unsigned long long)__popc(peers));
+    }
+}
+
+// per 4096-triplet tile: triplets with row in [r0, r1)
+__global__ void __launch_bounds__(PC_THREADS) k_panel_tile_count(const int *rows, int64_t nnz, int r0, int r1,
+                                                                 int *cnt) {
+    const int64_t base = (int64_t)blockIdx.x * PC_TILE;
+    int c = 0;
+    for (int k = threadIdx.x; k < PC_TILE; k += PC_THREADS) {
+        const int64_t i = base + k;
+        if (i < nnz) {
+            const int r = rows[i];
+            c += r >= r0 && r < r1;
+        }
+    }
+    c = __reduce_add_sync(FULL, c);
+    __shared__ int ws[PC_THREADS / 32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < PC_THREADS / 32; ++w) t += ws[w];
+        cnt[blockIdx.x] = t;
+    }
+}
+
+// stable scatter of the tile's in-panel triplets to off[tile] + rank
+template <typename W>
+__global__ void __launch_bounds__(PC_THREADS) k_panel_scatter(const int *rows, const int *cols, const W *vals,
+                                                              int64_t nnz, int r0, int r1, const int *off,
+                                                              int *orow, int *ocol, W *oval) {
+    __shared__ int total_s;
+    const int64_t base = (int64_t)blockIdx.x * PC_TILE + (int64_t)threadIdx.x * PC_ITEMS;
+    int c = 0;
+#pragma unroll
+    for (int j = 0; j < PC_ITEMS; ++j) {
+        const int64_t i = base + j;
+        if (i < nnz) {
+            const int r = rows[i];
+            c += r >= r0 && r < r1;
+        }
+    }
+    int pos = block_exclusive_scan(c, &total_s) + off[blockIdx.x];
+#pragma unroll
+    for (int j = 0; j < PC_ITEMS; ++j) {
+        const int64_t i = base + j;
+        if (i < nnz) {
+            const int r = rows[i];
+            if (r >= r0 && r < r1) {
+                orow[pos] = r - r0;
+                ocol[pos] = cols[i];
+                oval[pos] = vals[i];
+                ++pos;
+            }
+        }
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -608,6 +700,108 @@ int expand_rows(const int32_t *rowptr, int64_t m, int64_t nnz, int32_t *rows_out
     if (nnz == 0) return SPMV_OK;
     k_expand_rows<<<grid1d(nnz, 256), 256, 0, s>>>(rowptr, m, nnz, rows_out);
     SPMV_CUDA_TRY(cudaGetLastError());
+    return SPMV_OK;
+}
+
+int check_triplet_bounds(const int32_t *d_rows, const int32_t *d_cols, int64_t nnz, int64_t m, int64_t n,
+                         cudaStream_t s) {
+    if (nnz == 0) return SPMV_OK;
+    Tmp<unsigned> flags;
+    SPMV_TRY(flags.alloc(1, s));
+    SPMV_CUDA_TRY(cudaMemsetAsync(flags.p, 0, sizeof(unsigned), s));
+    k_check_triplets<<<grid1d(nnz, 256), 256, 0, s>>>(d_rows, d_cols, nnz, m, n, flags.p);
+    SPMV_CUDA_TRY(cudaGetLastError());
+    unsigned hflags = 0;
+    SPMV_CUDA_TRY(cudaMemcpyAsync(&hflags, flags.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    SPMV_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hflags & 1u) {
+        set_error("spmv_create: a triplet lies outside the %lld x %lld matrix", (long long)m, (long long)n);
+        return SPMV_ERR_INVALID;
+    }
+    return SPMV_OK;
+}
+
+int plan_panels(const int32_t *d_rows, int64_t nnz, int64_t m, int64_t limit, cudaStream_t s,
+                std::vector<int64_t> *bounds) {
+    const int64_t chunk = int64_t(1) << PANEL_CHUNK_SHIFT;
+    const int nchunks = (int)((m + chunk - 1) / chunk);
+    Tmp<unsigned long long> counts;
+    SPMV_TRY(counts.alloc(nchunks, s));
+    SPMV_CUDA_TRY(cudaMemsetAsync(counts.p, 0, sizeof(unsigned long long) * nchunks, s));
+    k_chunk_hist<<<grid1d(nnz, 256, 152 * 8), 256, sizeof(unsigned) * nchunks, s>>>(d_rows, nnz, nchunks, counts.p);
+    SPMV_CUDA_TRY(cudaGetLastError());
+    std::vector<unsigned long long> hc(nchunks);
+    SPMV_CUDA_TRY(cudaMemcpyAsync(hc.data(), counts.p, sizeof(unsigned long long) * nchunks,
+                                  cudaMemcpyDeviceToHost, s));
+    SPMV_CUDA_TRY(cudaStreamSynchronize(s));
+    bounds->assign(1, 0);
+    int64_t cur = 0;  // triplets in the open panel
+    for (int c = 0; c < nchunks; ++c) {
+        const int64_t lo = (int64_t)c * chunk, hi = std::min<int64_t>(m, lo + chunk);
+        if ((int64_t)hc[c] <= limit) {
+            if (cur > 0 && cur + (int64_t)hc[c] > limit) {
+                bounds->push_back(lo);
+                cur = 0;
+            }
+            cur += (int64_t)hc[c];
+            continue;
+        }
+        // a chunk over the limit: split it at 4-row groups
+        const int64_t ng = (hi - lo + 3) / 4;
+        Tmp<unsigned long long> g;
+        SPMV_TRY(g.alloc(ng, s));
+        SPMV_CUDA_TRY(cudaMemsetAsync(g.p, 0, sizeof(unsigned long long) * ng, s));
+        k_group_hist<<<grid1d(nnz, 256, 152 * 8), 256, 0, s>>>(d_rows, nnz, (int)lo, (int)hi, g.p);
+        SPMV_CUDA_TRY(cudaGetLastError());
+        std::vector<unsigned long long> hg(ng);
+        SPMV_CUDA_TRY(cudaMemcpyAsync(hg.data(), g.p, sizeof(unsigned long long) * ng, cudaMemcpyDeviceToHost, s));
+        SPMV_CUDA_TRY(cudaStreamSynchronize(s));
+        for (int64_t k = 0; k < ng; ++k) {
+            if ((int64_t)hg[k] > limit) {
+                set_error("spmv_create: rows %lld..%lld hold %llu triplets, more than one panel (%lld) holds",
+                          (long long)(lo + 4 * k), (long long)std::min<int64_t>(m, lo + 4 * k + 4) - 1,
+                          hg[k], (long long)limit);
+                return SPMV_ERR_UNSUPPORTED;
+            }
+            if (cur > 0 && cur + (int64_t)hg[k] > limit) {
+                bounds->push_back(lo + 4 * k);
+                cur = 0;
+            }
+            cur += (int64_t)hg[k];
+        }
+    }
+    bounds->push_back(m);
+    return SPMV_OK;
+}
+
+int gather_panel(const int32_t *d_rows, const int32_t *d_cols, const void *d_vals, size_t vs, int64_t nnz,
+                 int64_t r0, int64_t r1, int32_t **orow, int32_t **ocol, void **oval, int64_t *count,
+                 cudaStream_t s) {
+    *orow = *ocol = nullptr;
+    *oval = nullptr;
+    const int64_t ntiles = (nnz + PC_TILE - 1) / PC_TILE;
+    Tmp<int> cnt, off;
+    SPMV_TRY(cnt.alloc(ntiles, s));
+    SPMV_TRY(off.alloc(ntiles, s));
+    k_panel_tile_count<<<(unsigned)ntiles, PC_THREADS, 0, s>>>(d_rows, nnz, (int)r0, (int)r1, cnt.p);
+    SPMV_CUDA_TRY(cudaGetLastError());
+    int64_t total = 0;
+    SPMV_TRY(exclusive_scan(cnt.p, off.p, ntiles, s, &total));
+    *count = total;
+    SPMV_TRY(dalloc(orow, (size_t)total));
+    SPMV_TRY(dalloc(ocol, (size_t)total));
+    SPMV_TRY(dalloc_bytes(oval, vs * (size_t)std::max<int64_t>(total, 1)));
+    if (vs == 8)
+        k_panel_scatter<uint64_t><<<(unsigned)ntiles, PC_THREADS, 0, s>>>(
+            d_rows, d_cols, (const uint64_t *)d_vals, nnz, (int)r0, (int)r1, off.p, *orow, *ocol, (uint64_t *)*oval);
+    else if (vs == 4)
+        k_panel_scatter<uint32_t><<<(unsigned)ntiles, PC_THREADS, 0, s>>>(
+            d_rows, d_cols, (const uint32_t *)d_vals, nnz, (int)r0, (int)r1, off.p, *orow, *ocol, (uint32_t *)*oval);
+    else
+        k_panel_scatter<uint16_t><<<(unsigned)ntiles, PC_THREADS, 0, s>>>(
+            d_rows, d_cols, (const uint16_t *)d_vals, nnz, (int)r0, (int)r1, off.p, *orow, *ocol, (uint16_t *)*oval);
+    SPMV_CUDA_TRY(cudaGetLastError());
+    SPMV_CUDA_TRY(cudaStreamSynchronize(s));
     return SPMV_OK;
 }
 

@@ -77,7 +77,7 @@ __global__ void k_feat_rows(const int *rowptr, int64_t m, unsigned *hist, FeatAc
 // first column position >= c in the sorted column list [b, e)
 __device__ __forceinline__ int lower_col(const int *colidx, int b, int e, int c) {
     while (b < e) {
-        const int mid = (b + e) >> 1;
+        const int mid = b + ((e - b) >> 1);  // b + e overflows int past 2^30 offsets
         if (colidx[mid] < c) b = mid + 1; else e = mid;
     }
     return b;
@@ -97,7 +97,8 @@ __device__ __forceinline__ bool earlier_rows_hit(const int *rowptr, const int *c
 // One warp per row; lanes stride over the row's entries.  An entry opens a
 // new r x r block when no earlier entry of its block (earlier rows of the
 // block row, or the previous entry of its own row) lies in it.
-__global__ void k_feat_entries(const int *rowptr, const int *colidx, int64_t m, FeatAcc *acc) {
+// row0: the global index of local row 0 (a multiple of 4 for row panels)
+__global__ void k_feat_entries(const int *rowptr, const int *colidx, int64_t m, int64_t row0, FeatAcc *acc) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -107,7 +108,8 @@ __global__ void k_feat_entries(const int *rowptr, const int *colidx, int64_t m, 
         const int b = rowptr[i], e = rowptr[i + 1];
         for (int k = b + lane; k < e; k += 32) {
             const int j = colidx[k];
-            const int64_t d = i > j ? i - j : j - i;
+            const int64_t gi = row0 + i;
+            const int64_t d = gi > j ? gi - j : j - gi;
             sd += (unsigned long long)d;
             md = max(md, (int)d);
             dg += d == 0;
@@ -249,11 +251,18 @@ int compute_features(const spmv_matrix *h, double *d_out, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(hist, 0, hist_bytes, s);
     if (e == cudaSuccess) {
         k_feat_init<<<1, 1, 0, s>>>(acc);
-        if (m > 0) {
-            const int64_t blocks = (m + 255) / 256;
-            k_feat_rows<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(h->rowptr, m, hist, acc);
-            const int64_t wblocks = (m + 7) / 8;
-            k_feat_entries<<<(unsigned)(wblocks < 8192 ? wblocks : 8192), 256, 0, s>>>(h->rowptr, h->colidx, m, acc);
+        // a matrix held in row panels accumulates every panel into one set
+        const int np = h->npanels > 0 ? h->npanels : 1;
+        for (int p = 0; p < np; ++p) {
+            const spmv_matrix *q = h->npanels > 0 ? h->panels[p] : h;
+            const int64_t row0 = h->npanels > 0 ? h->panel_row0[p] : 0;
+            const int64_t mq = q->m;
+            if (mq == 0) continue;
+            const int64_t blocks = (mq + 255) / 256;
+            k_feat_rows<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(q->rowptr, mq, hist, acc);
+            const int64_t wblocks = (mq + 7) / 8;
+            k_feat_entries<<<(unsigned)(wblocks < 8192 ? wblocks : 8192), 256, 0, s>>>(q->rowptr, q->colidx, mq,
+                                                                                        row0, acc);
         }
         k_feat_finish<<<1, FIN_THREADS, 0, s>>>(hist, maxlen, m, h->n, h->nnz, acc, d_out);
         e = cudaGetLastError();

@@ -8,6 +8,7 @@
 
 #include <cstdarg>
 #include <cstdio>
+#include <vector>
 
 #include "spmv.h"
 
@@ -287,6 +288,12 @@ struct spmv_matrix {
     spmv::LongRows lng;
     // conjugate-gradient plan (cg.cu): scratch vectors and the solve's graph
     spmv::CgPlan *cg = nullptr;
+    // row panels: a matrix with more triplets than one handle indexes with
+    // int32 offsets is held as sub-handles over rows [panel_row0[p],
+    // panel_row0[p+1]); the parent then holds no arrays of its own
+    int32_t npanels = 0;
+    spmv_matrix **panels = nullptr;
+    int64_t *panel_row0 = nullptr;
 };
 
 namespace spmv {
@@ -304,6 +311,18 @@ int alloc_partials(Partials *p, int64_t units, int stride, int vt, cudaStream_t 
 void free_partials(Partials *p);
 int build_long_rows(spmv_matrix *h, const int32_t *rowptr, int64_t nrows, int64_t threshold, int64_t seg,
                     int stride, cudaStream_t s);
+
+// row panels (convert.cu): bounds check of every triplet; panel row bounds
+// (multiples of 4 rows, at most `limit` triplets each); stable copy of the
+// triplets of rows [r0, r1) with rows shifted by -r0 (device buffers the
+// caller frees with cudaFree)
+int check_triplet_bounds(const int32_t *d_rows, const int32_t *d_cols, int64_t nnz, int64_t m, int64_t n,
+                         cudaStream_t s);
+int plan_panels(const int32_t *d_rows, int64_t nnz, int64_t m, int64_t limit, cudaStream_t s,
+                std::vector<int64_t> *bounds);
+int gather_panel(const int32_t *d_rows, const int32_t *d_cols, const void *d_vals, size_t vs, int64_t nnz,
+                 int64_t r0, int64_t r1, int32_t **orow, int32_t **ocol, void **oval, int64_t *count,
+                 cudaStream_t s);
 
 // y = alpha A x + beta y in the handle's current format (api.cu)
 int run_product(const spmv_matrix *h, double alpha, const void *x, double beta, void *y, cudaStream_t s);

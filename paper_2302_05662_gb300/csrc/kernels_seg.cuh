@@ -208,7 +208,7 @@ __device__ __forceinline__ void csr_split_chunk(int64_t c, int64_t nnz, int64_t 
     if (cnt > 0 && a > 0) {  // largest row r in [H, H_next] with rowptr[r] <= a
         int lo = H, hi = __ldg(meta0 + c + 1);
         while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
+            const int mid = lo + ((hi - lo + 1) >> 1);  // lo + hi overflows int past 2^30 rows
             if (rp(mid) <= a) lo = mid; else hi = mid - 1;
         }
         cur = lo;
