@@ -124,8 +124,8 @@ int resolve_config(const spmv_matrix *h, const spmv_config *in, spmv_config *out
         set_error("config: unroll %d not in {1, 2, 4} (8 also for ELL, HYB, SELL)", c.unroll);
         return SPMV_ERR_INVALID;
     }
-    if (c.regcap != 32 && c.regcap != 64) {
-        set_error("config: regcap %d not in {32, 64}", c.regcap);
+    if (c.regcap != 32 && c.regcap != 64 && !(c.regcap == 48 && ell_family)) {
+        set_error("config: regcap %d not in {32, 64} (48 also for ELL, HYB, SELL)", c.regcap);
         return SPMV_ERR_INVALID;
     }
     if (c.carveout < -1 || c.carveout > 100) {

@@ -581,8 +581,10 @@ __global__ void k_sell_item_count(const int *sptr, int64_t nslices, int kmax, in
     }
 }
 
+// item j of a slice: its slice, the slot offset of its first column
+// (ptr[slice] + 32 j kmax), its column count, and the slice's item range
 __global__ void k_sell_item_fill(const int *sptr, int64_t nslices, int kmax, const int *off, int *it_slice,
-                                 int *it_k0, int *it_k1, int *it_c0, int *it_c1) {
+                                 int *it_base, int *it_len, int *it_c0, int *it_c1) {
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t sl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; sl < nslices; sl += stride) {
         const int width = (sptr[sl + 1] - sptr[sl]) / 32;
@@ -590,8 +592,8 @@ __global__ void k_sell_item_fill(const int *sptr, int64_t nslices, int kmax, con
         const int o = off[sl];
         for (int j = 0; j < n; ++j) {
             it_slice[o + j] = (int)sl;
-            it_k0[o + j] = j * kmax;
-            it_k1[o + j] = min((j + 1) * kmax, width);
+            it_base[o + j] = sptr[sl] + 32 * j * kmax;
+            it_len[o + j] = min((j + 1) * kmax, width) - j * kmax;
             it_c0[o + j] = o;
             it_c1[o + j] = o + n - 1;
         }

@@ -309,21 +309,21 @@ k_bsr_long(int64_t nseg, const int *__restrict__ seg_row, const int *__restrict_
 // ---------------------------------------------------------------------------
 template <typename V, typename T, int UNROLL, int REGCAP>
 __global__ void __launch_bounds__(1024) __maxnreg__(REGCAP)
-k_sell(int64_t m, int64_t nitems, const int *__restrict__ it_slice, const int *__restrict__ it_k0,
-       const int *__restrict__ it_k1, const int *__restrict__ it_c0, const int *__restrict__ it_c1,
-       const int *__restrict__ sptr, const int *__restrict__ col, const V *__restrict__ val,
-       const int *__restrict__ perm, const T *__restrict__ x, T *__restrict__ y, T alpha, T beta,
-       const PartialsT<T> P) {
+k_sell(int64_t m, int64_t nitems, const int *__restrict__ it_slice, const int *__restrict__ it_base,
+       const int *__restrict__ it_len, const int *__restrict__ it_c0, const int *__restrict__ it_c1,
+       const int *__restrict__ col, const V *__restrict__ val, const int *__restrict__ perm,
+       const T *__restrict__ x, T *__restrict__ y, T alpha, T beta, const PartialsT<T> P) {
     const Epi<T> ep(alpha, beta);
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t it = warp; it < nitems; it += nwarps) {
-        const int sl = __ldg(it_slice + it), k0 = __ldg(it_k0 + it), k1 = __ldg(it_k1 + it);
-        const int64_t base = (int64_t)__ldg(sptr + sl) + lane;
+        // an item is three independent loads: slice, slot offset, columns
+        const int sl = __ldg(it_slice + it), ib = __ldg(it_base + it), len = __ldg(it_len + it);
+        const int64_t base = (int64_t)ib + lane;
         T acc = T(0);
-        int k = k0;
-        for (; k + UNROLL <= k1; k += UNROLL) {
+        int k = 0;
+        for (; k + UNROLL <= len; k += UNROLL) {
             int c[UNROLL];
             T v[UNROLL], xv[UNROLL];
 #pragma unroll
@@ -337,7 +337,7 @@ k_sell(int64_t m, int64_t nitems, const int *__restrict__ it_slice, const int *_
             for (int u = 0; u < UNROLL; ++u)
                 if (c[u] >= 0) acc = fma(v[u], xv[u], acc);
         }
-        for (; k < k1; ++k) {
+        for (; k < len; ++k) {
             const int c = ld_s(col + base + 32LL * k);
             if (c >= 0) acc = fma(ld_val(val + base + 32LL * k), ld_x(x, c), acc);
         }

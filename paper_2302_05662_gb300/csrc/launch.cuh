@@ -109,8 +109,11 @@ int launch_ell_rc(const spmv_matrix *h, int64_t width, T alpha, const T *x, T be
 
 template <typename V, typename T, int U>
 int launch_ell(const spmv_matrix *h, int64_t width, T alpha, const T *x, T beta, T *y, cudaStream_t s) {
-    return h->cfg.regcap == 32 ? launch_ell_rc<V, T, U, 32>(h, width, alpha, x, beta, y, s)
-                               : launch_ell_rc<V, T, U, 64>(h, width, alpha, x, beta, y, s);
+    switch (h->cfg.regcap) {
+    case 32: return launch_ell_rc<V, T, U, 32>(h, width, alpha, x, beta, y, s);
+    case 48: return launch_ell_rc<V, T, U, 48>(h, width, alpha, x, beta, y, s);
+    default: return launch_ell_rc<V, T, U, 64>(h, width, alpha, x, beta, y, s);
+    }
 }
 
 template <int VT>
@@ -170,17 +173,19 @@ int launch_sell_rc(const spmv_matrix *h, T alpha, const T *x, T beta, T *y, cuda
     const LongRows &L = h->lng;
     const int64_t wpb = tpb / 32;
     const int grid = wave_grid((const void *)kern, tpb, (L.nseg + wpb - 1) / wpb, h->sm_count);
-    kern<<<grid, tpb, 0, s>>>(h->m, L.nseg, L.seg_row, L.seg_begin, L.seg_end, L.seg_c0, L.seg_c1, h->sell_ptr,
-                              h->sell_col, (const V *)h->sell_val, h->sell_perm, x, y, alpha, beta,
-                              PartialsT<T>::of(L.part));
+    kern<<<grid, tpb, 0, s>>>(h->m, L.nseg, L.seg_row, L.seg_begin, L.seg_end, L.seg_c0, L.seg_c1, h->sell_col,
+                              (const V *)h->sell_val, h->sell_perm, x, y, alpha, beta, PartialsT<T>::of(L.part));
     SPMV_LAUNCH_CHECK();
     return SPMV_OK;
 }
 
 template <typename V, typename T, int U>
 int launch_sell(const spmv_matrix *h, T alpha, const T *x, T beta, T *y, cudaStream_t s) {
-    return h->cfg.regcap == 32 ? launch_sell_rc<V, T, U, 32>(h, alpha, x, beta, y, s)
-                               : launch_sell_rc<V, T, U, 64>(h, alpha, x, beta, y, s);
+    switch (h->cfg.regcap) {
+    case 32: return launch_sell_rc<V, T, U, 32>(h, alpha, x, beta, y, s);
+    case 48: return launch_sell_rc<V, T, U, 48>(h, alpha, x, beta, y, s);
+    default: return launch_sell_rc<V, T, U, 64>(h, alpha, x, beta, y, s);
+    }
 }
 
 template <int VT>

@@ -54,7 +54,7 @@ def refine_space(best: dict):
     """Register cap x unroll x carveout around a winning point."""
     out = []
     ell_family = best.get("format", 0) in (B.FMT_ELL, B.FMT_HYB, B.FMT_SELL)
-    for rc in (32, 64):
+    for rc in ((32, 48, 64) if ell_family else (32, 64)):
         for u in ((1, 2, 4, 8) if ell_family else (1, 2, 4)):
             for cv in (-1, 0, 100):
                 d = dict(best)
