@@ -192,7 +192,7 @@ def reference_arm(args, rank):
 
 def workload_config(args):
     return {"workload": "format sweep over stencil27 128^3, poisson16 2^20, rmat s20 ef16, banded 2^20 w32, "
-                        "blockdiag4 2^20 (CSR/ELL/COO/HYB/BSR x launch parameters); step = one product per "
+                        "blockdiag4 2^20 (CSR/ELL/COO/HYB/BSR/SELL x launch parameters); step = one product per "
                         "matrix in the configuration the selector picks",
             "scale": args.scale, "value_dtype": args.dtype, "index_dtype": "int32", "alpha": 1.0, "beta": 0.0,
             "l2": "inputs larger than L2: each step streams ~2 GB; consecutive launches use different matrices"}

@@ -115,12 +115,11 @@ LAUNCH_CASES = (
     [("csr", dict(threads_per_row=t, unroll=u, regcap=rc))
      for t in (1, 2, 4, 8, 16, 32) for u in (1, 2, 4) for rc in (32, 64)]
     + [("csr_split", dict(unroll=u)) for u in (1, 2, 4)]
-    + [("ell", dict(unroll=u)) for u in (1, 2, 4)]
+    + [(nm, dict(unroll=u, regcap=rc)) for nm in ("ell", "hyb", "sell")
+       for u in (1, 2, 4, 8) for rc in (32, 48, 64)]
     + [("coo", dict(unroll=u)) for u in (1, 2, 4)]
-    + [("hyb", dict(unroll=u)) for u in (1, 2, 4)]
     + [("hyb", dict(hyb_ell_width=w)) for w in (1, 3, 100)]
     + [("bsr", dict(bsr_block=r, threads_per_row=s)) for r in (2, 4) for s in (1, 2, 4, 8)]
-    + [("sell", dict(unroll=u)) for u in (1, 2, 4)]
     + [(nm, dict(threads_per_block=t)) for nm in VARIANTS for t in (32, 1024)]
     + [(nm, dict(carveout=cv)) for nm in ("csr", "coo") for cv in (0, 50, 100, -1)]
 )
@@ -408,3 +407,24 @@ def test_set_config_switches_formats(oracle):
             assert rel_err(run(h, B.SPMV_F64, x, m=coo.m), want) <= 1e-13
     finally:
         B.spmv_destroy(h)
+
+
+def test_config_defaults_resolve_per_format_and_value_type():
+    """unroll/regcap 0 resolve per format and value type; out-of-family
+    values are refused without changing the handle."""
+    coo = matgen.laplacian_2d(32)
+    want = {(B.SPMV_F64, B.FMT_ELL): (2, 32), (B.SPMV_F32, B.FMT_ELL): (4, 32), (B.SPMV_BF16, B.FMT_HYB): (4, 32),
+            (B.SPMV_F64, B.FMT_SELL): (8, 64), (B.SPMV_F64, B.FMT_CSR): (2, 64), (B.SPMV_F32, B.FMT_COO): (2, 64)}
+    for (vt, fmt), (u, rc) in want.items():
+        h = create(coo, vt, B.make_config(format=fmt))
+        try:
+            c = B.spmv_get_config(h)
+            assert (c.unroll, c.regcap) == (u, rc), (vt, fmt)
+            for bad in (dict(format=B.FMT_CSR, regcap=48), dict(format=B.FMT_COO, unroll=8),
+                        dict(format=fmt, regcap=40), dict(format=fmt, unroll=3)):
+                with pytest.raises(B.SpmvError) as ei:
+                    B.spmv_set_config(h, B.make_config(**bad))
+                assert ei.value.status == -1
+                assert B.spmv_get_config(h).format == fmt          # refused before any re-pack
+        finally:
+            B.spmv_destroy(h)
