@@ -85,13 +85,11 @@ namespace {
 
 bool pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
 
-// Loads in flight per thread: ELL (and the ELL part of HYB) keeps four
-// column/value pairs in flight (measured fastest on regular matrices), the
-// other kernels two (or 8 entries per lane for the chunked kernels).
 // Loads in flight per lane when the configuration leaves unroll at 0.  ELL
 // and HYB with fp64 values keep two (a group of four fp64 loads needs more
 // registers than the 32-register variant has, and the loads then wait on
 // each other); fp32/bf16 keep four; SELL keeps eight with 64 registers.
+// Chunked kernels (COO, HYB tail, split CSR) take 4 x unroll entries a lane.
 int default_unroll(int format, int vt) {
     if (format == SPMV_FMT_SELL) return 8;
     if (format == SPMV_FMT_ELL || format == SPMV_FMT_HYB) return vt == SPMV_F64 ? 2 : 4;

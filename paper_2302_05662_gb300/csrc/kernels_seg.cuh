@@ -203,7 +203,12 @@ __device__ __forceinline__ void csr_split_chunk(int64_t c, int64_t nnz, int64_t 
     if ((int64_t)H + lane <= m) win[lane] = __ldg(rowptr + H + lane);
     if (lane == 0 && (int64_t)H + 32 <= m) win[32] = __ldg(rowptr + H + 32);
     __syncwarp();
-    auto rp = [&](int64_t r) -> int { return r - H <= 32 ? win[r - H] : __ldg(rowptr + r); };
+    // rows before H (the empty rows that lane 0 of chunk 0 walks from row 0)
+    // and rows past the window come from global memory
+    auto rp = [&](int64_t r) -> int {
+        const int64_t d = r - H;
+        return d >= 0 && d <= 32 ? win[d] : __ldg(rowptr + r);
+    };
     int cur = 0;
     if (cnt > 0 && a > 0) {  // largest row r in [H, H_next] with rowptr[r] <= a
         int lo = H, hi = __ldg(meta0 + c + 1);

@@ -421,7 +421,9 @@ def test_config_defaults_resolve_per_format_and_value_type():
             c = B.spmv_get_config(h)
             assert (c.unroll, c.regcap) == (u, rc), (vt, fmt)
             for bad in (dict(format=B.FMT_CSR, regcap=48), dict(format=B.FMT_COO, unroll=8),
-                        dict(format=fmt, regcap=40), dict(format=fmt, unroll=3)):
+                        dict(format=fmt, regcap=40), dict(format=fmt, unroll=3),
+                        dict(format=B.FMT_SELL, threads_per_row=2, unroll=8),
+                        dict(format=B.FMT_SELL, threads_per_row=4), dict(format=B.FMT_ELL, threads_per_row=2)):
                 with pytest.raises(B.SpmvError) as ei:
                     B.spmv_set_config(h, B.make_config(**bad))
                 assert ei.value.status == -1
