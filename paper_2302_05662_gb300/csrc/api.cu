@@ -460,7 +460,7 @@ int spmv_get_info(spmv_handle h, spmv_info *out) {
         break;
     case SPMV_FMT_ELL:
         out->ell_width = h->ell_width;
-        out->format_bytes = h->ell_width * h->ell_pitch * (vs + 4);
+        out->format_bytes = h->ell_width * h->ell_pitch * (vs + (h->ell_d16 ? 2 : 4));
         break;
     case SPMV_FMT_COO:
         out->format_bytes = h->nnz * (vs + 8);
@@ -468,7 +468,7 @@ int spmv_get_info(spmv_handle h, spmv_info *out) {
     case SPMV_FMT_HYB:
         out->ell_width = h->ell_width;
         out->hyb_coo_nnz = h->hyb_nnz;
-        out->format_bytes = h->ell_width * h->ell_pitch * (vs + 4) + h->hyb_nnz * (vs + 8);
+        out->format_bytes = h->ell_width * h->ell_pitch * (vs + (h->ell_d16 ? 2 : 4)) + h->hyb_nnz * (vs + 8);
         break;
     case SPMV_FMT_BSR:
         out->bsr_blocks = h->bsr_blocks;
@@ -510,7 +510,7 @@ int array_of(spmv_handle h, int32_t id, const void **ptr, int64_t *bytes) {
     case SPMV_ARR_CSR_COLIDX: *ptr = h->colidx; *bytes = 4 * h->nnz; break;
     case SPMV_ARR_CSR_VALS: *ptr = h->vals; *bytes = vs * h->nnz; break;
     case SPMV_ARR_ELL_COLIDX:
-        if (h->ell_col) { *ptr = h->ell_col; *bytes = 4 * h->ell_width * h->ell_pitch; }
+        if (h->ell_col || h->ell_d16) { *ptr = h->ell_col; *bytes = 4 * h->ell_width * h->ell_pitch; }
         break;
     case SPMV_ARR_ELL_VALS:
         if (h->ell_val) { *ptr = h->ell_val; *bytes = vs * h->ell_width * h->ell_pitch; }
@@ -587,6 +587,8 @@ int spmv_export(spmv_handle h, int32_t array_id, void *d_dst, int64_t bytes, voi
         set_error("spmv_export: NULL destination");
         return SPMV_ERR_INVALID;
     }
+    if (array_id == SPMV_ARR_ELL_COLIDX && h->ell_d16)  // 16-bit row offsets: export int32 columns
+        return decode_ell_columns(h, static_cast<int32_t *>(d_dst), (cudaStream_t)stream);
     SPMV_CUDA_TRY(cudaMemcpyAsync(d_dst, p, (size_t)have, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
     return SPMV_OK;
 }

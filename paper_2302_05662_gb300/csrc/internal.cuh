@@ -266,7 +266,8 @@ struct spmv_matrix {
     int32_t *coo_rows = nullptr;
     // ELL (also the ELL part of HYB)
     int64_t ell_width = 0, ell_pitch = 0;
-    int32_t *ell_col = nullptr;
+    int32_t *ell_col = nullptr;   // int32 columns, padding -1 ...
+    int16_t *ell_d16 = nullptr;   // ... or 16-bit column - row, padding INT16_MIN
     void *ell_val = nullptr;
     // HYB COO part
     int64_t hyb_nnz = 0;
@@ -278,7 +279,7 @@ struct spmv_matrix {
     int32_t *bsr_rowptr = nullptr, *bsr_col = nullptr;
     void *bsr_val = nullptr;
     // SELL: 32-row slices, column-major inside a slice, all rows stably
-    // sorted by descending length; work items = (slice, k range)
+    // sorted by descending length; work items = (slice, first slot, columns)
     int64_t sell_nslices = 0, sell_slots = 0;
     int32_t *sell_ptr = nullptr, *sell_col = nullptr, *sell_perm = nullptr;
     void *sell_val = nullptr;
@@ -305,6 +306,7 @@ int pack_format(spmv_matrix *h, const spmv_config &cfg, cudaStream_t s);
 void free_packed(spmv_matrix *h);
 int expand_rows(const int32_t *rowptr, int64_t m, int64_t nnz, int32_t *rows_out,
                 cudaStream_t s);
+int decode_ell_columns(const spmv_matrix *h, int32_t *d_out, cudaStream_t s);
 int ensure_seg_scratch(spmv_matrix *h, int items, bool split_csr, cudaStream_t s);
 int build_split_meta(const int32_t *rowptr, int64_t m, int64_t nnz, int C, int32_t *meta0, cudaStream_t s);
 int alloc_partials(Partials *p, int64_t units, int stride, int vt, cudaStream_t s);

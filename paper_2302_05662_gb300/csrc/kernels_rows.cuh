@@ -129,9 +129,17 @@ k_csr_long(int64_t nseg, const int *__restrict__ seg_row, const int *__restrict_
 // Index matrices).  Padding has column -1 and rows are left-packed, so a
 // thread stops at its first padding slot and reads no padding values.
 // ---------------------------------------------------------------------------
-template <typename V, typename T, int UNROLL, int REGCAP>
+// a stored ELL column: int32 (padding -1) or a 16-bit offset from the row
+// (padding INT16_MIN)
+__device__ __forceinline__ int ell_col_at(const int *p, int64_t r) { return ld_s(p); }
+__device__ __forceinline__ int ell_col_at(const int16_t *p, int64_t r) {
+    const int d = (int16_t)ld_s(reinterpret_cast<const unsigned short *>(p));
+    return d == INT16_MIN ? -1 : (int)r + d;
+}
+
+template <typename V, typename T, int UNROLL, int REGCAP, typename CI>
 __global__ void __launch_bounds__(1024) __maxnreg__(REGCAP)
-k_ell(int64_t m, int64_t width, int64_t pitch, const int *__restrict__ col, const V *__restrict__ val,
+k_ell(int64_t m, int64_t width, int64_t pitch, const CI *__restrict__ col, const V *__restrict__ val,
       const T *__restrict__ x, T *__restrict__ y, T alpha, T beta) {
     const Epi<T> ep(alpha, beta);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -145,7 +153,7 @@ k_ell(int64_t m, int64_t width, int64_t pitch, const int *__restrict__ col, cons
             int c[UNROLL];
             T v[UNROLL], xv[UNROLL];
 #pragma unroll
-            for (int u = 0; u < UNROLL; ++u) c[u] = ld_s(col + (k + u) * pitch + r);
+            for (int u = 0; u < UNROLL; ++u) c[u] = ell_col_at(col + (k + u) * pitch + r, r);
 #pragma unroll
             for (int u = 0; u < UNROLL; ++u) {
                 v[u] = ld_val(val + (k + u) * pitch + r);
@@ -158,7 +166,7 @@ k_ell(int64_t m, int64_t width, int64_t pitch, const int *__restrict__ col, cons
             }
         }
         for (; !done && k < width; ++k) {
-            const int c = ld_s(col + k * pitch + r);
+            const int c = ell_col_at(col + k * pitch + r, r);
             if (c < 0) break;
             acc += ld_val(val + k * pitch + r) * ld_x(x, c);
         }
@@ -302,7 +310,7 @@ k_bsr_long(int64_t nseg, const int *__restrict__ seg_row, const int *__restrict_
 // SELL (Section 2.3: slices of rows stored as small ELL matrices with a slice
 // pointer array).  Slices are 32 rows -- one warp, one lane per row -- of
 // rows sorted by descending length, so a slice's rows have similar lengths
-// and little padding.  A work item is (slice, k range): a
+// and little padding.  A work item is (slice, up to 256 columns): a
 // slice wider than 256 entries becomes several items whose per-row partials
 // are joined in item order, so a slice of power-law rows is not left to one
 // warp.

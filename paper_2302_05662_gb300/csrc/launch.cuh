@@ -96,15 +96,22 @@ int run_csr_vector_vt(const spmv_matrix *h, double alpha, const void *x, double 
 }
 
 // ----------------------------------- ELL -----------------------------------
-template <typename V, typename T, int U, int RC>
-int launch_ell_rc(const spmv_matrix *h, int64_t width, T alpha, const T *x, T beta, T *y, cudaStream_t s) {
-    auto kern = k_ell<V, T, U, RC>;
+template <typename V, typename T, int U, int RC, typename CI>
+int launch_ell_ci(const spmv_matrix *h, const CI *cols, int64_t width, T alpha, const T *x, T beta, T *y,
+                  cudaStream_t s) {
+    auto kern = k_ell<V, T, U, RC, CI>;
     const int tpb = h->cfg.threads_per_block;
     SPMV_TRY(apply_carveout((const void *)kern, h->cfg.carveout));
     const int grid = wave_grid((const void *)kern, tpb, (h->m + tpb - 1) / tpb, h->sm_count);
-    kern<<<grid, tpb, 0, s>>>(h->m, width, h->ell_pitch, h->ell_col, (const V *)h->ell_val, x, y, alpha, beta);
+    kern<<<grid, tpb, 0, s>>>(h->m, width, h->ell_pitch, cols, (const V *)h->ell_val, x, y, alpha, beta);
     SPMV_LAUNCH_CHECK();
     return SPMV_OK;
+}
+
+template <typename V, typename T, int U, int RC>
+int launch_ell_rc(const spmv_matrix *h, int64_t width, T alpha, const T *x, T beta, T *y, cudaStream_t s) {
+    if (h->ell_d16) return launch_ell_ci<V, T, U, RC, int16_t>(h, h->ell_d16, width, alpha, x, beta, y, s);
+    return launch_ell_ci<V, T, U, RC, int>(h, h->ell_col, width, alpha, x, beta, y, s);
 }
 
 template <typename V, typename T, int U>

@@ -152,6 +152,12 @@ def _edge_cases():
     out.append(("wide", matgen.random_coo(3, 4000, 3000, rng, integer_values=5)))
     out.append(("tall", matgen.random_coo(4000, 3, 3000, rng, integer_values=5)))
     out.append(("chunk_multiple", matgen.random_coo(256, 256, 8192, rng, integer_values=5)))
+    # ELL stores 16-bit column offsets while every |col - row| <= 32767
+    r = np.array([0, 1, 32767, 39999], np.int32)
+    out.append(("offset_32767", matgen.Coo(40000, 40000, r, np.array([32767, 1, 0, 7232], np.int32),
+                                           np.array([3.0, -2.0, 5.0, 1.0]))))
+    out.append(("offset_32768", matgen.Coo(40000, 40001, r, np.array([32768, 1, 0, 40000], np.int32),
+                                           np.array([3.0, -2.0, 5.0, 1.0]))))
     return out
 
 
@@ -430,3 +436,26 @@ def test_config_defaults_resolve_per_format_and_value_type():
                 assert B.spmv_get_config(h).format == fmt          # refused before any re-pack
         finally:
             B.spmv_destroy(h)
+
+
+@pytest.mark.parametrize("vt", VTS)
+def test_ell_column_offsets_16_bit_when_they_fit(vt):
+    """bf16 ELL keeps 2-byte column offsets iff every |col - row| <= 32767
+    (fp32/fp64 always int32): the format's byte count says which, and the
+    exported columns are the same int32 layout either way."""
+    import torch
+    vs = {B.SPMV_F64: 8, B.SPMV_F32: 4, B.SPMV_BF16: 2}[vt]
+    for case, fits in (("offset_32767", True), ("offset_32768", False)):
+        coo = dict(EDGE)[case]
+        h = create(coo, vt, cfg_of("ell"))
+        try:
+            info = B.spmv_get_info(h)
+            w = info.ell_width
+            col = _export(h, B.ARR_ELL_COLIDX, torch.int32).numpy()
+        finally:
+            B.spmv_destroy(h)
+        p = col.size // w
+        d16 = fits and vt == B.SPMV_BF16
+        assert info.format_bytes == w * p * (vs + (2 if d16 else 4)), case
+        got = {(int(r), int(c)) for k in range(w) for r, c in enumerate(col[k * p:(k + 1) * p]) if c >= 0}
+        assert got == set(zip(coo.rows.tolist(), coo.cols.tolist())), case
