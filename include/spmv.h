@@ -98,7 +98,9 @@ typedef enum {
  *   bsr_block         BSR block size r: 2 or 4 (default 4).
  *   hyb_ell_width     HYB ELL width; 0 applies the width rule (the largest
  *                     k such that at least max(4096, m/3) rows hold k or
- *                     more nonzeros).
+ *                     more nonzeros).  SELL: columns of a slice per work
+ *                     item, 8..65536 (0 = 128); wider slices are split into
+ *                     several items joined in order.
  * spmv_config_default() fills the defaults (carveout = -1; unroll and
  * regcap 0, resolved per format and value type when the configuration is
  * applied; spmv_get_config returns the resolved values).

@@ -138,6 +138,15 @@ int resolve_config(const spmv_matrix *h, const spmv_config *in, spmv_config *out
         set_error("config: negative hyb_ell_width");
         return SPMV_ERR_INVALID;
     }
+    if (c.format == SPMV_FMT_SELL) {  // SELL: columns of a slice per work item
+        // 128 balances warps best on power-law rows (R-MAT scale 20, fp64:
+        // 80.6 us at 128, 86.7 at 256, 95.9 at 64, 197 at 1024)
+        if (c.hyb_ell_width == 0) c.hyb_ell_width = 128;
+        if (c.hyb_ell_width < 8 || c.hyb_ell_width > 65536) {
+            set_error("config: SELL columns per work item %d not in [8, 65536]", c.hyb_ell_width);
+            return SPMV_ERR_INVALID;
+        }
+    }
     switch (c.format) {
     case SPMV_FMT_CSR:
         if (c.threads_per_row == 0) c.threads_per_row = default_tpr(h);

@@ -1189,9 +1189,9 @@ int pack_bsr(spmv_matrix *h, int r, cudaStream_t s) {
 }  // namespace
 
 namespace {
-constexpr int SELL_KMAX = 256;  // slice entries per work item
 
-int pack_sell(spmv_matrix *h, cudaStream_t s) {
+// kmax: columns of a slice per work item (wider slices become several items)
+int pack_sell(spmv_matrix *h, int kmax, cudaStream_t s) {
     const int64_t m = h->m;
     const int64_t nslices = (m + 31) / 32;
     const size_t vs = value_size(h->vt);
@@ -1248,17 +1248,17 @@ int pack_sell(spmv_matrix *h, cudaStream_t s) {
     Tmp<int> cnt, off;
     SPMV_TRY(cnt.alloc(nslices, s));
     SPMV_TRY(off.alloc(nslices, s));
-    k_sell_item_count<<<grid1d(nslices, 256), 256, 0, s>>>(h->sell_ptr, nslices, SELL_KMAX, cnt.p);
+    k_sell_item_count<<<grid1d(nslices, 256), 256, 0, s>>>(h->sell_ptr, nslices, kmax, cnt.p);
     int64_t nitems = 0;
     SPMV_TRY(exclusive_scan(cnt.p, off.p, nslices, s, &nitems));
     L.nseg = nitems;
-    L.threshold = SELL_KMAX;
+    L.threshold = kmax;
     SPMV_TRY(dalloc(&L.seg_row, (size_t)nitems));
     SPMV_TRY(dalloc(&L.seg_begin, (size_t)nitems));
     SPMV_TRY(dalloc(&L.seg_end, (size_t)nitems));
     SPMV_TRY(dalloc(&L.seg_c0, (size_t)nitems));
     SPMV_TRY(dalloc(&L.seg_c1, (size_t)nitems));
-    k_sell_item_fill<<<grid1d(nslices, 256), 256, 0, s>>>(h->sell_ptr, nslices, SELL_KMAX, off.p, L.seg_row,
+    k_sell_item_fill<<<grid1d(nslices, 256), 256, 0, s>>>(h->sell_ptr, nslices, kmax, off.p, L.seg_row,
                                                            L.seg_begin, L.seg_end, L.seg_c0, L.seg_c1);
     SPMV_CUDA_TRY(cudaGetLastError());
     SPMV_TRY(alloc_partials(&L.part, nitems, 32, h->vt, s));
@@ -1357,7 +1357,7 @@ int pack_format(spmv_matrix *h, const spmv_config &cfg, cudaStream_t s) {
         break;
     }
     case SPMV_FMT_SELL:
-        SPMV_TRY(pack_sell(h, s));
+        SPMV_TRY(pack_sell(h, cfg.hyb_ell_width, s));
         break;
     case SPMV_FMT_BSR: {
         SPMV_TRY(pack_bsr(h, cfg.bsr_block, s));

@@ -310,10 +310,10 @@ k_bsr_long(int64_t nseg, const int *__restrict__ seg_row, const int *__restrict_
 // SELL (Section 2.3: slices of rows stored as small ELL matrices with a slice
 // pointer array).  Slices are 32 rows -- one warp, one lane per row -- of
 // rows sorted by descending length, so a slice's rows have similar lengths
-// and little padding.  A work item is (slice, up to 256 columns): a
-// slice wider than 256 entries becomes several items whose per-row partials
-// are joined in item order, so a slice of power-law rows is not left to one
-// warp.
+// and little padding.  A work item covers at most the item width (128
+// columns by default) of one slice: a wider slice becomes several items whose
+// per-row partials are joined in item order, so a slice of power-law rows is
+// not left to one warp.
 // ---------------------------------------------------------------------------
 template <typename V, typename T, int UNROLL, int REGCAP>
 __global__ void __launch_bounds__(1024) __maxnreg__(REGCAP)

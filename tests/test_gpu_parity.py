@@ -119,6 +119,7 @@ LAUNCH_CASES = (
        for u in (1, 2, 4, 8) for rc in (32, 48, 64)]
     + [("coo", dict(unroll=u)) for u in (1, 2, 4)]
     + [("hyb", dict(hyb_ell_width=w)) for w in (1, 3, 100)]
+    + [("sell", dict(hyb_ell_width=w)) for w in (8, 24, 64, 1024)]
     + [("bsr", dict(bsr_block=r, threads_per_row=s)) for r in (2, 4) for s in (1, 2, 4, 8)]
     + [(nm, dict(threads_per_block=t)) for nm in VARIANTS for t in (32, 1024)]
     + [(nm, dict(carveout=cv)) for nm in ("csr", "coo") for cv in (0, 50, 100, -1)]
