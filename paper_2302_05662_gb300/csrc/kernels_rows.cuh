@@ -325,7 +325,12 @@ k_sell(int64_t m, int64_t nitems, const int *__restrict__ it_slice, const int *_
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t it = warp; it < nitems; it += nwarps) {
+    // items come widest slice first; rounds alternate direction over the
+    // warps (warp w takes item w of round 0, item 2N-1-w of round 1, ...), so
+    // the warps that drew the widest items draw the narrowest next
+    for (int64_t j = 0; j * nwarps < nitems; ++j) {
+        const int64_t it = j * nwarps + ((j & 1) ? nwarps - 1 - warp : warp);
+        if (it >= nitems) continue;
         // an item is three independent loads: slice, slot offset, columns
         const int sl = __ldg(it_slice + it), ib = __ldg(it_base + it), len = __ldg(it_len + it);
         const int64_t base = (int64_t)ib + lane;
