@@ -11,8 +11,21 @@ y <- A x of every matrix in its selected configuration; value = 2 * (sum of
 nnz) per step / step time, in GFLOP/s.  Every step streams ~2 GB, far more
 than the 129 MB L2, and consecutive launches use different matrices.
 
+Besides the timed step the JSON line carries: per_kernel (time, warm-cache
+time, fraction of the measured HBM peak per matrix), roofline (dominant
+kernel, DRAM traffic from the committed ncu capture), e2e (x uploaded and y
+downloaded every step, copies overlapping the products), selector (choice
+vs exhaustive best, overheads, the run-time gate's predictions against
+measurements), format_sweep (best time of every format per matrix, against
+the format-independent byte model and the format's own bytes), batched (512
+uneven fp32 matrices in one graph-captured launch), cg (conjugate gradients
+on the 27-point Laplacian, default CSR vs the gate's choice), energy (NVML
+energy counter, report-only), clocks, gpu_launches and cpu_baseline.
+
 --impl reference times the fp64 CPU oracle instead (the timed baseline of
-this method; there is no other reference implementation).
+this method; there is no other reference implementation).  --traffic runs
+one product per (matrix, format) in NVTX ranges for an ncu DRAM-bytes
+capture and exits.
 """
 from __future__ import annotations
 
