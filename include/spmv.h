@@ -90,8 +90,8 @@ typedef enum {
  *   regcap            register cap per thread, 32 (the paper's
  *                     maxrregcount knob) or 64 (the ceiling that keeps
  *                     1024-thread blocks launchable); 48 also for ELL, HYB
- *                     and SELL.  0 = default: 32 for ELL and HYB, 64
- *                     otherwise.
+ *                     and SELL.  0 = default: 32 for ELL and HYB with fp64
+ *                     values, 64 otherwise.
  *   carveout          preferred shared-memory carveout in percent (0..100),
  *                     or -1 to leave the driver default (Section 4 item 3).
  *                     Zero means 0 % (maximum L1), not "default".

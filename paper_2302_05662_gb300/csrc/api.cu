@@ -96,9 +96,13 @@ int default_unroll(int format, int vt) {
     return 2;
 }
 
-// Register cap when the configuration leaves regcap at 0: ELL and HYB run
-// the 32-register variant (two 1024-thread blocks per SM), the rest 64.
-int default_regcap(int format) { return format == SPMV_FMT_ELL || format == SPMV_FMT_HYB ? 32 : 64; }
+// Register cap when the configuration leaves regcap at 0: fp64 ELL and HYB
+// run the 32-register variant (two 1024-thread blocks per SM); fp32/bf16 ELL
+// and HYB (two rows per thread, twice the loads in flight) and the other
+// formats 64.
+int default_regcap(int format, int vt) {
+    return (format == SPMV_FMT_ELL || format == SPMV_FMT_HYB) && vt == SPMV_F64 ? 32 : 64;
+}
 
 // Fills defaults and validates; returns SPMV_ERR_INVALID on a bad field.
 int resolve_config(const spmv_matrix *h, const spmv_config *in, spmv_config *out) {
@@ -107,7 +111,7 @@ int resolve_config(const spmv_matrix *h, const spmv_config *in, spmv_config *out
     if (in) c = *in;
     if (c.threads_per_block == 0) c.threads_per_block = 256;
     if (c.unroll == 0) c.unroll = default_unroll(c.format, h->vt);
-    if (c.regcap == 0) c.regcap = default_regcap(c.format);
+    if (c.regcap == 0) c.regcap = default_regcap(c.format, h->vt);
     if (c.bsr_block == 0) c.bsr_block = 4;
     if (c.format < SPMV_FMT_CSR || c.format > SPMV_FMT_SELL) {
         set_error("config: unknown format %d", c.format);

@@ -174,6 +174,79 @@ k_ell(int64_t m, int64_t width, int64_t pitch, const CI *__restrict__ col, const
     }
 }
 
+// Two adjacent rows per thread (fp32/bf16 values): rows r, r + 1 sit side by
+// side in every column-major slice, so each load fetches both rows' entries
+// in one 8-byte (int32 columns, fp32 values) or 4-byte (16-bit offsets, bf16
+// values) access and a warp request covers 64 rows instead of 32.
+__device__ __forceinline__ void ell_cols2(const int *p, int64_t r, int &a, int &b) {
+    const int2 w = ld_s(reinterpret_cast<const int2 *>(p));
+    a = w.x;
+    b = w.y;
+}
+__device__ __forceinline__ void ell_cols2(const int16_t *p, int64_t r, int &a, int &b) {
+    const uint32_t w = (uint32_t)ld_s(reinterpret_cast<const int *>(p));
+    const int d0 = (int16_t)(w & 0xffffu), d1 = (int16_t)(w >> 16);
+    a = d0 == INT16_MIN ? -1 : (int)r + d0;
+    b = d1 == INT16_MIN ? -1 : (int)r + 1 + d1;
+}
+__device__ __forceinline__ void ell_vals2(const float *p, float &a, float &b) {
+    const float2 w = ld_s(reinterpret_cast<const float2 *>(p));
+    a = w.x;
+    b = w.y;
+}
+__device__ __forceinline__ void ell_vals2(const __nv_bfloat16 *p, float &a, float &b) {
+    const uint32_t w = (uint32_t)ld_s(reinterpret_cast<const int *>(p));
+    a = bf16lo(w);
+    b = bf16hi(w);
+}
+
+template <typename V, typename T, int UNROLL, int REGCAP, typename CI>
+__global__ void __launch_bounds__(1024) __maxnreg__(REGCAP)
+k_ell2(int64_t m, int64_t width, int64_t pitch, const CI *__restrict__ col, const V *__restrict__ val,
+       const T *__restrict__ x, T *__restrict__ y, T alpha, T beta) {
+    const Epi<T> ep(alpha, beta);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // pairs of rows up to the pitch (a multiple of 32): padding rows past m
+    // hold padding slots, so every pair load stays inside the arrays
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; 2 * q < m; q += stride) {
+        const int64_t r = 2 * q;
+        T acc0 = T(0), acc1 = T(0);
+        bool done0 = false, done1 = false;
+        int64_t k = 0;
+        for (; !(done0 && done1) && k + UNROLL <= width; k += UNROLL) {
+            int c0[UNROLL], c1[UNROLL];
+            T v0[UNROLL], v1[UNROLL], x0[UNROLL], x1[UNROLL];
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) ell_cols2(col + (k + u) * pitch + r, r, c0[u], c1[u]);
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) {
+                ell_vals2(val + (k + u) * pitch + r, v0[u], v1[u]);
+                x0[u] = ld_x(x, c0[u] >= 0 ? c0[u] : 0);
+                x1[u] = ld_x(x, c1[u] >= 0 ? c1[u] : 0);
+            }
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) {
+                if (c0[u] >= 0) acc0 = fma(v0[u], x0[u], acc0);
+                else done0 = true;
+                if (c1[u] >= 0) acc1 = fma(v1[u], x1[u], acc1);
+                else done1 = true;
+            }
+        }
+        for (; !(done0 && done1) && k < width; ++k) {
+            int c0, c1;
+            T v0, v1;
+            ell_cols2(col + k * pitch + r, r, c0, c1);
+            ell_vals2(val + k * pitch + r, v0, v1);
+            if (c0 >= 0) acc0 = fma(v0, ld_x(x, c0), acc0);
+            else done0 = true;
+            if (c1 >= 0) acc1 = fma(v1, ld_x(x, c1), acc1);
+            else done1 = true;
+        }
+        ep.store(y, r, acc0);
+        if (r + 1 < m) ep.store(y, r + 1, acc1);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // BSR with R x R row-major blocks (the blocked ELL of Section 2.3 stored by
 // block rows).  A group of R*S lanes owns a block row: lane (s, i) takes

@@ -3,6 +3,8 @@
 // the ~150 kernel variants compile in parallel.
 #pragma once
 
+#include <type_traits>
+
 #include "kernels_rows.cuh"
 #include "kernels_seg.cuh"
 
@@ -99,11 +101,19 @@ int run_csr_vector_vt(const spmv_matrix *h, double alpha, const void *x, double 
 template <typename V, typename T, int U, int RC, typename CI>
 int launch_ell_ci(const spmv_matrix *h, const CI *cols, int64_t width, T alpha, const T *x, T beta, T *y,
                   cudaStream_t s) {
-    auto kern = k_ell<V, T, U, RC, CI>;
     const int tpb = h->cfg.threads_per_block;
-    SPMV_TRY(apply_carveout((const void *)kern, h->cfg.carveout));
-    const int grid = wave_grid((const void *)kern, tpb, (h->m + tpb - 1) / tpb, h->sm_count);
-    kern<<<grid, tpb, 0, s>>>(h->m, width, h->ell_pitch, cols, (const V *)h->ell_val, x, y, alpha, beta);
+    if constexpr (!std::is_same<V, double>::value) {  // fp32/bf16: two rows per thread
+        auto kern = k_ell2<V, T, U, RC, CI>;
+        SPMV_TRY(apply_carveout((const void *)kern, h->cfg.carveout));
+        const int64_t pairs = (h->m + 1) / 2;
+        const int grid = wave_grid((const void *)kern, tpb, (pairs + tpb - 1) / tpb, h->sm_count);
+        kern<<<grid, tpb, 0, s>>>(h->m, width, h->ell_pitch, cols, (const V *)h->ell_val, x, y, alpha, beta);
+    } else {
+        auto kern = k_ell<V, T, U, RC, CI>;
+        SPMV_TRY(apply_carveout((const void *)kern, h->cfg.carveout));
+        const int grid = wave_grid((const void *)kern, tpb, (h->m + tpb - 1) / tpb, h->sm_count);
+        kern<<<grid, tpb, 0, s>>>(h->m, width, h->ell_pitch, cols, (const V *)h->ell_val, x, y, alpha, beta);
+    }
     SPMV_LAUNCH_CHECK();
     return SPMV_OK;
 }

@@ -420,7 +420,7 @@ def test_config_defaults_resolve_per_format_and_value_type():
     """unroll/regcap 0 resolve per format and value type; out-of-family
     values are refused without changing the handle."""
     coo = matgen.laplacian_2d(32)
-    want = {(B.SPMV_F64, B.FMT_ELL): (2, 32), (B.SPMV_F32, B.FMT_ELL): (4, 32), (B.SPMV_BF16, B.FMT_HYB): (4, 32),
+    want = {(B.SPMV_F64, B.FMT_ELL): (2, 32), (B.SPMV_F32, B.FMT_ELL): (4, 64), (B.SPMV_BF16, B.FMT_HYB): (4, 64),
             (B.SPMV_F64, B.FMT_SELL): (8, 64), (B.SPMV_F64, B.FMT_CSR): (2, 64), (B.SPMV_F32, B.FMT_COO): (2, 64)}
     for (vt, fmt), (u, rc) in want.items():
         h = create(coo, vt, B.make_config(format=fmt))
