@@ -4,7 +4,7 @@ Workload: the format sweep over five synthetic matrices (27-point stencil
 128^3, Poisson(16) random rows n = 2^20, R-MAT scale 20 edge factor 16,
 banded n = 2^20 half-width 32, block-diagonal 4x4 n = 2^20), fp64 values and
 vectors, int32 indices.  For each matrix the exhaustive sweep over format x
-launch parameters is run first (the judge of the selector; its per-format
+launch parameters is run first (what the selector is scored against; its per-format
 best times are reported in format_sweep), then the trained selector picks a
 configuration on the device (spmv_select).  One timed step = one product
 y <- A x of every matrix in its selected configuration; value = 2 * (sum of

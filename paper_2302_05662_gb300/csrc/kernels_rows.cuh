@@ -398,9 +398,9 @@ k_sell(int64_t m, int64_t nitems, const int *__restrict__ it_slice, const int *_
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    // items come widest slice first; rounds alternate direction over the
-    // warps (warp w takes item w of round 0, item 2N-1-w of round 1, ...), so
-    // the warps that drew the widest items draw the narrowest next
+    // items come widest slice first; passes over the warps alternate
+    // direction (warp w takes item w of pass 0, item 2N-1-w of pass 1, ...),
+    // so the warps that drew the widest items draw the narrowest next
     for (int64_t j = 0; j * nwarps < nitems; ++j) {
         const int64_t it = j * nwarps + ((j & 1) ? nwarps - 1 - warp : warp);
         if (it >= nitems) continue;
