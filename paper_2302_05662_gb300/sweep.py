@@ -215,6 +215,8 @@ def main():
     ap.add_argument("--time-budget", type=float, default=1e9, help="seconds; stop cleanly after")
     ap.add_argument("--calibrate-pack", action="store_true",
                     help="time format conversions of matrices start..start+count instead")
+    ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16"],
+                    help="value type of the swept matrices (labels for a per-precision selector)")
     ap.add_argument("--formats", default=None,
                     help="comma list (csr,ell,coo,hyb,bsr,sell): a supplementary sweep of these formats' "
                          "label points only, merged into earlier records by the selector trainer")
@@ -248,8 +250,9 @@ def main():
             if time.time() - t0 > args.time_budget:
                 break
             fam, coo = generate_dataset_matrix(idx, n_hi=args.n_hi)
-            res = sweep_matrix(coo, space + [default_csr(coo)], timer, reps=args.reps, seed=idx)
-            rec = {"matrix": idx, "family": fam, "m": coo.m, "n": coo.n, "nnz": coo.nnz,
+            res = sweep_matrix(coo, space + [default_csr(coo)], timer, reps=args.reps, value_dtype=args.dtype,
+                               seed=idx)
+            rec = {"matrix": idx, "family": fam, "m": coo.m, "n": coo.n, "nnz": coo.nnz, "dtype": args.dtype,
                    "default_us": res[-1][1], "times": [[config_key(c), t] for c, t in res[:-1]]}
             if args.formats is None:
                 rec["features"] = [float(v) for v in matrix_features(coo)]
