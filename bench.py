@@ -12,7 +12,9 @@ nnz) per step / step time, in GFLOP/s.  Every step streams ~2 GB, far more
 than the 129 MB L2, and consecutive launches use different matrices.
 
 Besides the timed step the JSON line carries: per_kernel (time, warm-cache
-time, fraction of the measured HBM peak per matrix), roofline (dominant
+time, fraction of the measured HBM peak per matrix, and the time of a
+device copy moving the same bytes in the same order: the size-matched
+floor that launch and ramp costs put under small kernels), roofline (dominant
 kernel, DRAM traffic from the committed ncu capture), e2e (x uploaded and y
 downloaded every step, copies overlapping the products), selector (choice
 vs exhaustive best, overheads, the run-time gate's predictions against
@@ -89,6 +91,34 @@ def measured_peak():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return FALLBACK_HBM_GBS, "fallback"
+
+
+def copy_floor_us(torch, stream, sizes, steps=100):
+    """Size-matched floor: for each byte count, a device-to-device copy that
+    reads half of it and writes the other half, in the step's order and
+    timed like the step's kernels (CUDA events around each copy on the
+    launching stream, each copy preceded by the previous one).  A small
+    kernel pays the same launch and memory-pipeline ramp as a copy of its
+    size, so kernel time against this floor separates that fixed cost from
+    the kernel's own efficiency.  Returns the mean microseconds per copy."""
+    bufs = [(torch.empty(max(16, b // 2), dtype=torch.uint8, device="cuda"),
+             torch.empty(max(16, b // 2), dtype=torch.uint8, device="cuda")) for b in sizes]
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in sizes]
+          for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            for src, dst in bufs:
+                dst.copy_(src)
+        for s in range(steps):
+            for i, (src, dst) in enumerate(bufs):
+                ev[s][i][0].record(stream)
+                dst.copy_(src)
+                ev[s][i][1].record(stream)
+    torch.cuda.synchronize()
+    out = [sum(ev[s][i][0].elapsed_time(ev[s][i][1]) for s in range(steps)) * 1e3 / steps
+           for i in range(len(sizes))]
+    del bufs
+    return out
 
 
 def byte_model(m, n, nnz, vt_size, vec_size, beta_nonzero=False):
@@ -694,14 +724,17 @@ def ours(args, world, rank, local):
         torch.cuda.synchronize()
         warm_us.append(w0.elapsed_time(w1) * 1e3 / 50)
 
+    copy_us = copy_floor_us(torch, stream, [p["bytes"] for p in mats])
+
     peak, peak_kind = measured_peak()
     per_kernel = []
-    for p, ms, wu in zip(mats, per_ms, warm_us):
+    for p, ms, wu, cu in zip(mats, per_ms, warm_us, copy_us):
         gbs = p["bytes"] / (ms * 1e-3) / 1e9
         per_kernel.append({"matrix": p["matrix"], "kernel": fmt_name(p["cfg"]), "config": p["cfg"],
                            "source": p["source"], "us": round(ms * 1e3, 2), "warm_cache_us": round(wu, 2),
                            "gflops": round(2 * p["nnz"] / (ms * 1e-3) / 1e9, 1), "gbs": round(gbs, 1),
-                           "frac": round(gbs / peak, 4)})
+                           "frac": round(gbs / peak, 4), "copy_floor_us": round(cu, 2),
+                           "frac_of_copy": round(cu / (ms * 1e3), 4)})
     dom = max(range(len(mats)), key=lambda i: per_ms[i])
     dp = mats[dom]
     achieved = dp["bytes"] / (per_ms[dom] * 1e-3) / 1e9
