@@ -324,13 +324,8 @@ def tune_matrix(B, sweep, h, coo, x, y, timer, reps):
 def batched_section(B, matgen, torch, count=512, seed=7, steps=20):
     """512 uneven fp32 matrices: one graph-captured persistent launch (after
     the autotuner) against one spmv_run per matrix."""
-    import math
-    rng = np.random.default_rng(seed)
     hs, xs, ys, nnz = [], [], [], 0
-    for i in range(count):
-        fam = matgen.FAMILIES[i % len(matgen.FAMILIES)]
-        n = int(math.exp(rng.uniform(math.log(1e3), math.log(2e5))))
-        coo = matgen.family_matrix(fam, n, seed=5000 + i, jitter=True)
+    for i, coo in matgen.batched_workload(count, seed):
         r = torch.from_numpy(coo.rows).cuda()
         c = torch.from_numpy(coo.cols).cuda()
         v = torch.from_numpy(coo.vals).cuda().float()

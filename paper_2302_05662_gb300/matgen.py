@@ -367,3 +367,18 @@ def workload_matrices(scale: str = "full", seed: int = 1, only=None):
         coo = fn(np.random.default_rng(seed * 1000 + k))
         coo.name = name
         yield name, coo
+
+
+def batched_workload(count: int = 512, seed: int = 7):
+    """The batched workload: `count` matrices with n log-uniform in
+    [10^3, 2*10^5] (one draw per matrix from `seed`), families cycling
+    through FAMILIES, jittered parameters, matrix i from seed 5000 + i.
+    Yields (i, Coo) lazily; the x of matrix i is dense_vector(n, 9000 + i)."""
+    import math
+    rng = np.random.default_rng(seed)
+    for i in range(count):
+        fam = FAMILIES[i % len(FAMILIES)]
+        n = int(math.exp(rng.uniform(math.log(1e3), math.log(2e5))))
+        coo = family_matrix(fam, n, seed=5000 + i, jitter=True)
+        coo.name = f"batch{i}_{fam}"
+        yield i, coo

@@ -117,3 +117,42 @@ def test_batch_rejects_mixed_types():
     finally:
         B.spmv_destroy(h1)
         B.spmv_destroy(h2)
+
+
+def test_batch_fullsize_512_fp32_tuned(oracle):
+    """The benchmark's batched workload at full size (512 fp32 matrices, n
+    log-uniform in [10^3, 2*10^5], about 5.2*10^8 nonzeros), after the
+    autotuner, in the graph the benchmark replays: every matrix against the
+    oracle on the inputs the device holds (fp32-rounded values and x).  The
+    matrices are generated again for the check so host memory stays small."""
+    import torch
+    hs, xs, ys = [], [], []
+    try:
+        for i, coo in matgen.batched_workload():
+            hs.append(create(coo, B.SPMV_F32))
+            xs.append(torch.from_numpy(matgen.dense_vector(coo.n, 9000 + i)).float().cuda())
+            ys.append(torch.full((coo.m,), float("nan"), dtype=torch.float32, device="cuda"))
+        count = len(hs)
+        assert count == 512
+        b = B.spmv_batch_create(hs, np.ones(count), xs, np.zeros(count), ys)
+        try:
+            B.spmv_batch_tune(b)
+            for y in ys:
+                y.fill_(float("nan"))
+            B.spmv_batch_launch(b)
+            torch.cuda.synchronize()
+            modes, items, tpb = B.spmv_batch_get_plan(b, count)
+            assert 0 in modes.tolist() and any(m != 0 for m in modes.tolist())
+        finally:
+            B.spmv_batch_destroy(b)
+        worst = 0.0
+        for i, coo in matgen.batched_workload():
+            got = ys[i].cpu().double().numpy()
+            want = oracle_for(oracle, coo, B.SPMV_F32, matgen.dense_vector(coo.n, 9000 + i))
+            err = rel_err(got, want)
+            assert err <= TOL[B.SPMV_F32], (i, coo.name, err)
+            worst = max(worst, err)
+        assert worst > 0.0          # fp32 accumulation differs from the fp64 oracle somewhere
+    finally:
+        for h in hs:
+            B.spmv_destroy(h)
