@@ -35,7 +35,7 @@ int cuda_status(cudaError_t e, const char *what) {
 namespace {
 std::mutex g_attr_mu;
 std::map<std::pair<const void *, int>, int> g_occ;
-std::map<const void *, int> g_carve;
+std::map<std::pair<const void *, int>, int> g_carve;  // (kernel, device): function attributes are per device
 }  // namespace
 
 int resident_blocks(const void *kernel, int threads) {
@@ -56,16 +56,19 @@ int resident_blocks(const void *kernel, int threads) {
 
 int apply_carveout(const void *kernel, int carveout) {
     std::lock_guard<std::mutex> lk(g_attr_mu);
-    auto it = g_carve.find(kernel);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const auto key = std::make_pair(kernel, dev);
+    auto it = g_carve.find(key);
     const int current = it == g_carve.end() ? -1 : it->second;
     if (current == carveout) return SPMV_OK;
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                                          carveout < 0 ? (int)cudaSharedmemCarveoutDefault : carveout);
     if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute(carveout)");
-    g_carve[kernel] = carveout;
-    // resident block counts may change with the carveout
+    g_carve[key] = carveout;
+    // resident block counts of this kernel on this device may change with the carveout
     for (auto i = g_occ.begin(); i != g_occ.end();) {
-        if (i->first.first == kernel) i = g_occ.erase(i);
+        if (i->first.first == kernel && i->first.second % 64 == dev) i = g_occ.erase(i);
         else ++i;
     }
     return SPMV_OK;
