@@ -50,3 +50,17 @@ def test_bf16_rounding_ties_to_even():
     assert r[4] == 1.0 + 2.0 ** -7                  # just above the tie
     assert np.array_equal(matgen.round_to_f32(np.array([0.1])),
                           np.array([np.float32(0.1)], dtype=np.float64))
+
+
+def test_batched_workload_families_sizes_and_seeds():
+    """The batch cycles through the families with n log-uniform in
+    [10^3, 2*10^5] (after each family's snapping) and is reproducible."""
+    import itertools
+    first = list(itertools.islice(matgen.batched_workload(), 10))
+    again = list(itertools.islice(matgen.batched_workload(), 10))
+    for (i, a), (j, b) in zip(first, again):
+        assert i == j and a.name == b.name and np.array_equal(a.cols, b.cols) and np.array_equal(a.vals, b.vals)
+    for i, coo in first:
+        assert coo.name == f"batch{i}_{matgen.FAMILIES[i % 5]}"
+        assert 500 <= coo.m <= 300_000 and coo.nnz > 0 and _sorted_unique(coo)
+    assert len(list(itertools.islice(matgen.batched_workload(count=3), 10))) == 3
