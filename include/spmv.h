@@ -348,7 +348,8 @@ SPMV_API int spmv_select(spmv_handle h, spmv_config *out_cfg, double *h_features
  * per row; h_modes may be NULL), the items and the block size.
  * spmv_batch_run: create + launch + destroy in one call (synchronises).
  * Errors: SPMV_ERR_INVALID (NULL arrays or handles, mixed value types),
- * SPMV_ERR_OOM, SPMV_ERR_CUDA.
+ * SPMV_ERR_UNSUPPORTED (a handle held in row panels), SPMV_ERR_OOM,
+ * SPMV_ERR_CUDA.
  */
 typedef struct spmv_batch *spmv_batch_handle;
 
