@@ -67,3 +67,49 @@ def test_host_argument_errors(lib):
     assert lib.spmv_run(None, 1.0, None, 0.0, None, None) == -1
     assert lib.spmv_destroy(None) == 0
     assert lib.spmv_get_info(None, None) == -1
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include <string.h>
+#include "spmv.h"
+
+int main(void) {
+    spmv_config cfg;
+    spmv_handle h = NULL;
+    spmv_config_default(&cfg, SPMV_FMT_SELL);
+    if (cfg.format != SPMV_FMT_SELL || cfg.threads_per_block != 256) return 1;
+    if (spmv_create(&h, -1, 3, 0, NULL, NULL, NULL, SPMV_F64, NULL, NULL) != SPMV_ERR_INVALID) return 2;
+    if (h != NULL || strstr(spmv_last_error(), "negative") == NULL) return 3;
+    if (spmv_get_panel_limit() != SPMV_PANEL_LIMIT_MAX) return 4;
+    if (spmv_set_panel_limit(0) != SPMV_ERR_INVALID) return 5;
+    if (spmv_destroy(NULL) != SPMV_OK) return 6;
+    printf("ok\n");
+    return 0;
+}
+"""
+
+
+def test_header_is_plain_c_and_a_c_program_links(lib, tmp_path):
+    """include/spmv.h compiles as strict C99 and as C++; a C program links
+    against the library and runs its host-only paths (no GPU touched)."""
+    import shutil
+    import subprocess
+    inc = os.path.join(ROOT, "include")
+    for compiler, std in (("gcc", "-std=c99"), ("g++", "-std=c++17")):
+        if shutil.which(compiler) is None:
+            pytest.skip(f"{compiler} not installed")
+        lang = "c" if compiler == "gcc" else "c++"
+        r = subprocess.run([compiler, std, "-x", lang, "-pedantic", "-Wall", "-Wextra", "-Werror", "-fsyntax-only",
+                            "-I", inc, os.path.join(inc, "spmv.h")], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
+    src = tmp_path / "abi.c"
+    src.write_text(C_PROGRAM)
+    exe = tmp_path / "abi"
+    libdir = os.path.dirname(binding.LIB_PATH)
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", inc, str(src), "-o", str(exe), "-L", libdir,
+                        "-l:" + os.path.basename(binding.LIB_PATH), "-Wl,-rpath," + libdir],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stdout, r.stderr)
