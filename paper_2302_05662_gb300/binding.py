@@ -15,6 +15,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_build", "libspmv_gb300.so")
 
 SPMV_OK = 0
+SPMV_ERR_INVALID = -1
 STATUS_NAMES = {0: "SPMV_OK", -1: "SPMV_ERR_INVALID", -2: "SPMV_ERR_OOM", -3: "SPMV_ERR_CUDA",
                 -4: "SPMV_ERR_UNSUPPORTED", -5: "SPMV_ERR_BOUNDS", -6: "SPMV_ERR_TIMEOUT"}
 SPMV_F64, SPMV_F32, SPMV_BF16 = 0, 1, 2
@@ -153,7 +154,51 @@ def _stream(stream):
 
 
 def _ptr(t):
-    return None if t is None else t.data_ptr()
+    """Device address of a dense CUDA tensor (None gives NULL).  Host tensors
+    and strided views are refused before the call: the library reads every
+    buffer as a dense device array."""
+    if t is None:
+        return None
+    if not getattr(t, "is_cuda", False):
+        raise SpmvError(SPMV_ERR_INVALID, "expected a CUDA tensor (a device buffer)")
+    if not t.is_contiguous():
+        raise SpmvError(SPMV_ERR_INVALID, "expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _vec(t, need: int, vt: int, what: str):
+    """Device address of a vector the library reads or writes `need` entries
+    of, in the vector type of value type vt (fp64 for fp64 values, else
+    fp32)."""
+    if t is None:
+        if need > 0:
+            raise SpmvError(SPMV_ERR_INVALID, f"{what}: NULL where {need} entries are needed")
+        return None
+    import torch
+    want = torch.float64 if vt == SPMV_F64 else torch.float32
+    if t.dtype != want:
+        raise SpmvError(SPMV_ERR_INVALID, f"{what}: dtype {t.dtype}, the matrix's vectors are {want}")
+    if t.numel() < need:
+        raise SpmvError(SPMV_ERR_INVALID, f"{what}: {t.numel()} entries, {need} needed")
+    return _ptr(t)
+
+
+def _triplets(rows, cols, vals):
+    """(nnz, value type, pointers) of device COO triplets: int32 rows and
+    columns and fp64/fp32/bf16 values of one length."""
+    import torch
+    if rows is None or cols is None or vals is None:
+        if any(t is not None and t.numel() > 0 for t in (rows, cols, vals)):
+            raise SpmvError(SPMV_ERR_INVALID, "triplets: rows, cols and vals must all be given")
+        return 0, SPMV_F64, None, None, None
+    if rows.dtype != torch.int32 or cols.dtype != torch.int32:
+        raise SpmvError(SPMV_ERR_INVALID, "triplets: rows and cols must be int32")
+    if vals.dtype not in (torch.float64, torch.float32, torch.bfloat16):
+        raise SpmvError(SPMV_ERR_INVALID, f"triplets: value dtype {vals.dtype} is not fp64, fp32 or bf16")
+    nnz = int(rows.numel())
+    if cols.numel() != nnz or vals.numel() != nnz:
+        raise SpmvError(SPMV_ERR_INVALID, "triplets: rows, cols and vals differ in length")
+    return nnz, value_type_of(vals.dtype), _ptr(rows), _ptr(cols), _ptr(vals)
 
 
 def value_type_of(dtype) -> int:
@@ -178,10 +223,10 @@ def spmv_create(m: int, n: int, rows, cols, vals, cfg: spmv_config | None = None
     """Handle from device COO triplets (int32 rows/cols, f64/f32/bf16 vals)."""
     lib = load_library()
     h = _VP()
-    nnz = int(rows.numel()) if rows is not None else 0
-    vt = value_type_of(vals.dtype)
-    _check(lib.spmv_create(ctypes.byref(h), int(m), int(n), nnz, _ptr(rows), _ptr(cols), _ptr(vals), vt,
+    nnz, vt, rp, cp, vp = _triplets(rows, cols, vals)
+    _check(lib.spmv_create(ctypes.byref(h), int(m), int(n), nnz, rp, cp, vp, vt,
                            ctypes.byref(cfg) if cfg is not None else None, _stream(stream)))
+    _shapes[h.value] = (int(m), int(n), vt)
     return h.value
 
 
@@ -201,9 +246,28 @@ def spmv_get_info(h: int) -> spmv_info:
     return info
 
 
+# (m, n, value type) of the handles this process created: the vector checks
+# of spmv_run and friends then cost a dictionary lookup, not a library call
+_shapes: dict = {}
+
+
+def _shape(h: int):
+    s = _shapes.get(h)
+    if s is None:
+        info = spmv_get_info(h)
+        s = _shapes[h] = (int(info.m), int(info.n), int(info.value_type))
+    return s
+
+
 def spmv_run(h: int, alpha: float, x, beta: float, y, stream=None):
-    """y <- alpha*A*x + beta*y on the device (x, y: torch CUDA tensors)."""
-    _check(load_library().spmv_run(h, float(alpha), _ptr(x), float(beta), _ptr(y), _stream(stream)))
+    """y <- alpha*A*x + beta*y on the device (x, y: torch CUDA tensors of
+    the matrix's vector type, at least n and m entries)."""
+    if h:
+        m, n, vt = _shape(h)
+        xp, yp = _vec(x, n, vt, "x"), _vec(y, m, vt, "y")
+    else:
+        xp, yp = _ptr(x), _ptr(y)
+    _check(load_library().spmv_run(h, float(alpha), xp, float(beta), yp, _stream(stream)))
 
 
 def spmv_export_bytes(h: int, array_id: int) -> int:
@@ -267,8 +331,19 @@ def _batch_arrays(handles, alphas, xs, betas, ys):
     hs = (_VP * n)(*handles)
     al = np.ascontiguousarray(alphas, dtype=np.float64)
     be = np.ascontiguousarray(betas, dtype=np.float64)
-    xp = (_VP * n)(*[_ptr(x) for x in xs])
-    yp = (_VP * n)(*[_ptr(y) for y in ys])
+    if len(xs) != n or len(ys) != n or al.size != n or be.size != n:
+        raise SpmvError(SPMV_ERR_INVALID, "batch: handles, alphas, xs, betas and ys differ in length")
+    px, py = [], []
+    for i, h in enumerate(handles):
+        if h:
+            m, n_, vt = _shape(h)
+            px.append(_vec(xs[i], n_, vt, f"xs[{i}]"))
+            py.append(_vec(ys[i], m, vt, f"ys[{i}]"))
+        else:
+            px.append(_ptr(xs[i]))
+            py.append(_ptr(ys[i]))
+    xp = (_VP * n)(*px)
+    yp = (_VP * n)(*py)
     return n, hs, al, be, xp, yp
 
 
@@ -321,7 +396,15 @@ def spmv_cg(h: int, b, x, tol: float, maxit: int, rho=None, stream=None) -> spmv
     on entry and the last iterate on return; rho (optional float64 device
     tensor of maxit + 1 entries) receives r_k.r_k per iteration."""
     out = spmv_cg_result()
-    _check(load_library().spmv_cg(h, _ptr(b), _ptr(x), float(tol), int(maxit), _ptr(rho), ctypes.byref(out),
+    if h:
+        m, n, vt = _shape(h)
+        bp, xp = _vec(b, m, vt, "b"), _vec(x, n, vt, "x")
+    else:
+        bp, xp = _ptr(b), _ptr(x)
+    rp = None
+    if rho is not None:
+        rp = _vec(rho, max(0, int(maxit)) + 1, SPMV_F64, "rho")
+    _check(load_library().spmv_cg(h, bp, xp, float(tol), int(maxit), rp, ctypes.byref(out),
                                   _stream(stream)))
     return out
 
@@ -342,12 +425,13 @@ NOALLOC_MAX_NNZ = 1 << 25
 def spmv_coo_run_noalloc(m: int, n: int, rows, cols, vals, alpha: float, x, beta: float, y, stream=None):
     """y <- alpha*A*x + beta*y from row-sorted device COO triplets, with no
     device allocation (the library's fixed scratch array is used)."""
-    nnz = int(rows.numel()) if rows is not None else 0
-    _check(load_library().spmv_coo_run_noalloc(int(m), int(n), nnz, _ptr(rows), _ptr(cols), _ptr(vals),
-                                               value_type_of(vals.dtype), float(alpha), _ptr(x), float(beta),
-                                               _ptr(y), _stream(stream)))
+    nnz, vt, rp, cp, vp = _triplets(rows, cols, vals)
+    _check(load_library().spmv_coo_run_noalloc(int(m), int(n), nnz, rp, cp, vp, vt, float(alpha),
+                                               _vec(x, int(n), vt, "x"), float(beta),
+                                               _vec(y, int(m), vt, "y"), _stream(stream)))
 
 
 def spmv_destroy(h: int):
     if h:
+        _shapes.pop(h, None)
         _check(load_library().spmv_destroy(h))

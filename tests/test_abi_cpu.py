@@ -113,3 +113,57 @@ def test_header_is_plain_c_and_a_c_program_links(lib, tmp_path):
     assert r.returncode == 0, r.stderr
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
     assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stdout, r.stderr)
+
+
+class _FakeDeviceTensor:
+    """Stands in for a CUDA tensor in the binding's host-side checks."""
+    is_cuda = True
+
+    def __init__(self, n, dtype, contiguous=True):
+        self.n, self.dtype, self.contiguous = n, dtype, contiguous
+
+    def numel(self):
+        return self.n
+
+    def is_contiguous(self):
+        return self.contiguous
+
+    def data_ptr(self):
+        return 1 << 20
+
+
+def test_binding_refuses_host_strided_short_and_mistyped_buffers():
+    """Buffers that would send kernels to host memory or past an end are
+    refused in the binding, with SPMV_ERR_INVALID, before any call."""
+    import torch
+    E = binding.SpmvError
+    F = _FakeDeviceTensor
+    with pytest.raises(E) as ei:
+        binding._ptr(torch.zeros(3))
+    assert ei.value.status == -1 and "CUDA" in str(ei.value)
+    with pytest.raises(E):
+        binding._ptr(F(8, torch.float64, contiguous=False))
+    assert binding._ptr(None) is None and binding._ptr(F(8, torch.float64)) == 1 << 20
+    assert binding._vec(F(8, torch.float64), 8, binding.SPMV_F64, "x") == 1 << 20
+    assert binding._vec(F(8, torch.float32), 5, binding.SPMV_BF16, "x") == 1 << 20
+    assert binding._vec(None, 0, binding.SPMV_F64, "y") is None
+    for t, need, vt in ((F(7, torch.float64), 8, binding.SPMV_F64),      # too short
+                        (F(8, torch.float32), 8, binding.SPMV_F64),      # fp32 vector, fp64 matrix
+                        (F(8, torch.float64), 8, binding.SPMV_F32),      # fp64 vector, fp32 matrix
+                        (F(8, torch.bfloat16), 8, binding.SPMV_BF16),    # bf16 matrices take fp32 vectors
+                        (None, 1, binding.SPMV_F64)):
+        with pytest.raises(E) as ei:
+            binding._vec(t, need, vt, "x")
+        assert ei.value.status == -1
+    i32, i64 = torch.int32, torch.int64
+    for r, c, v in ((F(4, i64), F(4, i32), F(4, torch.float64)),
+                    (F(4, i32), F(3, i32), F(4, torch.float64)),
+                    (F(4, i32), F(4, i32), F(4, torch.float16)),
+                    (F(4, i32), None, F(4, torch.float64))):
+        with pytest.raises(E):
+            binding._triplets(r, c, v)
+    assert binding._triplets(F(4, i32), F(4, i32), F(4, torch.bfloat16))[:2] == (4, binding.SPMV_BF16)
+    assert binding._triplets(None, None, None)[0] == 0
+    with pytest.raises(E) as ei:            # host vectors never reach the library
+        binding.spmv_run(None, 1.0, torch.zeros(3), 0.0, torch.zeros(3))
+    assert ei.value.status == -1
