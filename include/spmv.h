@@ -178,7 +178,8 @@ SPMV_API int spmv_get_info(spmv_handle h, spmv_info *out);
  * d_x holds n values and d_y m values, of type double (SPMV_F64) or float
  * (SPMV_F32, SPMV_BF16); both are caller-owned device buffers, and x must
  * not overlap y.  beta == 0 means y is not read (NaN in y is ignored).
- * One or two kernel launches on `stream`; never synchronises.
+ * One or two kernel launches on `stream` per row panel (one panel unless
+ * the matrix has more triplets than the panel limit); never synchronises.
  * Errors: SPMV_ERR_INVALID for a NULL handle or a NULL vector with a
  * nonzero size; SPMV_ERR_CUDA if a launch fails.
  */
