@@ -52,9 +52,15 @@ typedef enum {
     SPMV_ERR_OOM = -2,         /* device allocation failed                 */
     SPMV_ERR_CUDA = -3,        /* a CUDA runtime call failed               */
     SPMV_ERR_UNSUPPORTED = -4, /* valid but not supported (e.g. ELL width) */
-    SPMV_ERR_BOUNDS = -5,      /* a device-side bounds check fired         */
-    SPMV_ERR_TIMEOUT = -6      /* a bounded device wait gave up            */
+    SPMV_ERR_BOUNDS = -5,      /* reserved: no entry point returns it       */
+    SPMV_ERR_TIMEOUT = -6      /* reserved: no kernel waits on another      */
 } spmv_status;
+/* Out-of-range triplets are found by a device check in spmv_create and
+ * reported as SPMV_ERR_INVALID.  No kernel spins on a flag: rows shared by
+ * work units are joined by whichever unit arrives last, the batched kernel
+ * takes work from one atomic counter, and conjugate gradients stop through
+ * a graph conditional node; so no call can wait on the device without
+ * bound, and the last two codes are kept only for ABI stability. */
 
 typedef enum { SPMV_F64 = 0, SPMV_F32 = 1, SPMV_BF16 = 2 } spmv_dtype;
 
