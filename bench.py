@@ -121,6 +121,48 @@ def copy_floor_us(torch, stream, sizes, steps=100):
     return out
 
 
+def gather_floor_us(B, torch, stream, mats, steps=100):
+    """Gather floor of every matrix (spmv_probe_gather_floor: the product's
+    bytes with ideal streaming access and its x gathers, no floating-point
+    instruction), launched in the step's order and timed like the step's
+    kernels.  Returns the mean microseconds per launch."""
+    sh = stream.cuda_stream
+    for _ in range(3):
+        for p in mats:
+            B.spmv_probe_gather_floor(p["h"], p["x"], p["y"], sh)
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in mats]
+          for _ in range(steps)]
+    for s_ in range(steps):
+        for i, p in enumerate(mats):
+            ev[s_][i][0].record(stream)
+            B.spmv_probe_gather_floor(p["h"], p["x"], p["y"], sh)
+            ev[s_][i][1].record(stream)
+    torch.cuda.synchronize()
+    return [sum(ev[s_][i][0].elapsed_time(ev[s_][i][1]) for s_ in range(steps)) * 1e3 / steps
+            for i in range(len(mats))]
+
+
+def fp64_fma_peak(B, torch, stream, iterations=4096, reps=5):
+    """Measured fp64 ceiling of this GPU: a full wave of independent fp64 FMA
+    chains (spmv_probe_fp64_fma), best of `reps` launches after two warm-up
+    launches, in TFLOP/s (2 flops per FMA)."""
+    sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+    sh = stream.cuda_stream
+    for _ in range(2):
+        B.spmv_probe_fp64_fma(iterations, sink, sh)
+    best = None
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        count = B.spmv_probe_fp64_fma(iterations, sink, sh)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) * 1e-3
+        rate = 2.0 * count / t / 1e12
+        best = rate if best is None else max(best, rate)
+    return best
+
+
 def byte_model(m, n, nnz, vt_size, vec_size, beta_nonzero=False):
     """Algorithmic bytes of one product: values + column indices of every
     nonzero, the m+1 row pointers, x once and y once (twice if beta != 0)."""
@@ -324,7 +366,7 @@ def tune_matrix(B, sweep, h, coo, x, y, timer, reps):
 def batched_section(B, matgen, torch, count=512, seed=7, steps=20):
     """512 uneven fp32 matrices: one graph-captured persistent launch (after
     the autotuner) against one spmv_run per matrix."""
-    hs, xs, ys, nnz = [], [], [], 0
+    hs, xs, ys, nnz, nbytes = [], [], [], 0, 0
     for i, coo in matgen.batched_workload(count, seed):
         r = torch.from_numpy(coo.rows).cuda()
         c = torch.from_numpy(coo.cols).cuda()
@@ -333,6 +375,7 @@ def batched_section(B, matgen, torch, count=512, seed=7, steps=20):
         xs.append(torch.from_numpy(matgen.dense_vector(coo.n, 9000 + i)).float().cuda())
         ys.append(torch.zeros(coo.m, dtype=torch.float32, device="cuda"))
         nnz += coo.nnz
+        nbytes += byte_model(coo.m, coo.n, coo.nnz, 4, 4)
     ones, zeros = np.ones(count), np.zeros(count)
     b = B.spmv_batch_create(hs, ones, xs, zeros, ys)
     stream = torch.cuda.current_stream()
@@ -359,15 +402,32 @@ def batched_section(B, matgen, torch, count=512, seed=7, steps=20):
             for k in range(count):
                 B.spmv_run(hs[k], 1.0, xs[k], 0.0, ys[k], sh)
         t_sep = timed(separate)
+
+        # the same 512 launches captured once into a CUDA graph: what one
+        # kernel per matrix costs without the host's per-call overhead
+        g = torch.cuda.CUDAGraph()
+        separate()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g):
+            cap = torch.cuda.current_stream().cuda_stream
+            for k in range(count):
+                B.spmv_run(hs[k], 1.0, xs[k], 0.0, ys[k], cap)
+        t_sep_graph = timed(g.replay)
+        del g
     finally:
         B.spmv_batch_destroy(b)
         for h in hs:
             B.spmv_destroy(h)
+    peak, peak_kind = measured_peak()
     return {"matrices": count, "nnz": nnz, "value_dtype": "f32",
             "graph_ms": round(t_graph, 4), "graph_gflops": round(2 * nnz / (t_graph * 1e-3) / 1e9, 2),
+            "algorithmic_bytes": nbytes, "gbs": round(nbytes / (t_graph * 1e-3) / 1e9, 1),
+            "frac": round(nbytes / (t_graph * 1e-3) / 1e9 / peak, 4), "peak_source": peak_kind,
             "separate_launches_ms": round(t_sep, 4),
             "separate_gflops": round(2 * nnz / (t_sep * 1e-3) / 1e9, 2),
             "speedup": round(t_sep / t_graph, 3),
+            "separate_launches_graph_ms": round(t_sep_graph, 4),
+            "speedup_vs_graph_of_launches": round(t_sep_graph / t_graph, 3),
             "plan": {"items": items, "threads_per_block": tpb,
                      "split_matrices": int((modes == 0).sum()),
                      "vector_matrices": int((modes != 0).sum())}}
@@ -720,16 +780,23 @@ def ours(args, world, rank, local):
         warm_us.append(w0.elapsed_time(w1) * 1e3 / 50)
 
     copy_us = copy_floor_us(torch, stream, [p["bytes"] for p in mats])
+    gather_us = gather_floor_us(B, torch, stream, mats)
+    fp64_tflops = fp64_fma_peak(B, torch, stream)
 
     peak, peak_kind = measured_peak()
     per_kernel = []
-    for p, ms, wu, cu in zip(mats, per_ms, warm_us, copy_us):
+    for p, ms, wu, cu, gu in zip(mats, per_ms, warm_us, copy_us, gather_us):
         gbs = p["bytes"] / (ms * 1e-3) / 1e9
-        per_kernel.append({"matrix": p["matrix"], "kernel": fmt_name(p["cfg"]), "config": p["cfg"],
-                           "source": p["source"], "us": round(ms * 1e3, 2), "warm_cache_us": round(wu, 2),
-                           "gflops": round(2 * p["nnz"] / (ms * 1e-3) / 1e9, 1), "gbs": round(gbs, 1),
-                           "frac": round(gbs / peak, 4), "copy_floor_us": round(cu, 2),
-                           "frac_of_copy": round(cu / (ms * 1e3), 4)})
+        tflops = 2 * p["nnz"] / (ms * 1e-3) / 1e12
+        row = {"matrix": p["matrix"], "kernel": fmt_name(p["cfg"]), "config": p["cfg"],
+               "source": p["source"], "us": round(ms * 1e3, 2), "warm_cache_us": round(wu, 2),
+               "gflops": round(tflops * 1e3, 1), "gbs": round(gbs, 1),
+               "frac": round(gbs / peak, 4), "copy_floor_us": round(cu, 2),
+               "frac_of_copy": round(cu / (ms * 1e3), 4), "gather_floor_us": round(gu, 2),
+               "frac_of_gather_floor": round(gu / (ms * 1e3), 4)}
+        if vt == B.SPMV_F64:   # one fp64 FMA per nonzero: the second ceiling
+            row["fp64_frac"] = round(tflops / fp64_tflops, 4)
+        per_kernel.append(row)
     dom = max(range(len(mats)), key=lambda i: per_ms[i])
     dp = mats[dom]
     achieved = dp["bytes"] / (per_ms[dom] * 1e-3) / 1e9
@@ -739,7 +806,18 @@ def ours(args, world, rank, local):
                 "traffic_source": tr[1] if tr else None,
                 "kernel": f"{fmt_name(dp['cfg'])} on {dp['matrix']}",
                 "algorithmic_bytes_per_launch": dp["bytes"], "peak_source": peak_kind,
-                "time_share": round(per_ms[dom] / sum(per_ms), 3)}
+                "time_share": round(per_ms[dom] / sum(per_ms), 3),
+                "fp64_fma_peak_tflops": round(fp64_tflops, 4)}
+    if vt == B.SPMV_F64:
+        # fp64 values: one FMA per nonzero against the measured fp64 FMA
+        # rate; the roofline is whichever ceiling the kernel is closer to
+        fp_ach = 2 * dp["nnz"] / (per_ms[dom] * 1e-3) / 1e12
+        roofline["hbm_frac"] = roofline["frac"]
+        roofline["fp64_frac"] = round(fp_ach / fp64_tflops, 4)
+        if fp_ach / fp64_tflops > achieved / peak:
+            roofline.update({"bound": "alu", "achieved": round(fp_ach, 4), "peak": round(fp64_tflops, 4),
+                             "unit": "TFLOP/s", "frac": round(fp_ach / fp64_tflops, 4),
+                             "peak_source": "measured fp64 FMA microkernel (spmv_probe_fp64_fma)"})
     for fs in format_sweep:
         fs["frac"] = round(fs["gbs"] / peak, 4)
         fs["format_frac"] = round(fs["format_gbs"] / peak, 4)

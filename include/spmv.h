@@ -251,22 +251,29 @@ SPMV_API int spmv_export(spmv_handle h, int32_t array_id, void *d_dst, int64_t b
  * d_rows, d_cols, d_vals hold nnz triplets with rows in nondecreasing order
  * (columns in any order; repeated pairs are summed), values of value_type;
  * d_x has n entries and d_y m entries (double for SPMV_F64, else float).
+ * d_rows, d_cols and d_vals must start on 16-byte boundaries (the kernel
+ * reads them with 16-byte vector loads; cudaMalloc'd arrays and tensors
+ * that start their storage always do, a view that starts mid-array may not).
  * All arrays stay owned by the caller.  beta == 0 means y is not read.
  *
- * Errors: SPMV_ERR_UNSUPPORTED when nnz > SPMV_NOALLOC_MAX_NNZ or m, n >=
- * 2^31; SPMV_ERR_INVALID for bad sizes, NULL arrays, or triplets that are
- * out of range or not sorted by row (checked on the device before any
- * product is formed; y is then left unchanged); SPMV_ERR_CUDA.
+ * Errors: SPMV_ERR_UNSUPPORTED when nnz > SPMV_NOALLOC_MAX_NNZ, m or n >=
+ * 2^31, or `stream` is being captured into a graph; SPMV_ERR_INVALID for
+ * bad sizes, NULL arrays, triplet arrays not 16-byte aligned (checked on
+ * the host, nothing launched), or triplets that are out of range or not
+ * sorted by row (checked on the device before any product is formed); in
+ * every error case y is left unchanged; SPMV_ERR_CUDA.
  *
- * The call synchronises `stream` once, to read that check.  The first call
- * on a device does the set-up: it looks up the device address of the fixed
- * array on that device (once per device, with the device current), and the
+ * A call with nnz > 0 synchronises `stream` once, to read the triplet
+ * check.  The first call on a device does the set-up: it looks up the
+ * device address of the fixed array on that device (once per device, with
+ * the device current; the address is kept for the life of the process, so
+ * do not use this entry point on a device after cudaDeviceReset), and the
  * CUDA driver loads the library's kernels then if it has not yet done so;
  * make that first call before any stream capture.  Later calls allocate
- * nothing.  Every call shares the one array, and each call
- * clears the parts that must start at zero, so calls are correct one after
- * another; calls whose kernels overlap on the GPU (other threads, other
- * streams) race on the array and give wrong results.
+ * nothing.  Every call shares the one array, and each call clears the parts
+ * that must start at zero, so calls are correct one after another; calls
+ * whose kernels overlap on the GPU (other threads, other streams) race on
+ * the array and give wrong results.
  */
 SPMV_API int spmv_coo_run_noalloc(int64_t m, int64_t n, int64_t nnz,
                                   const int32_t *d_rows, const int32_t *d_cols,

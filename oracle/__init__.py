@@ -15,6 +15,10 @@ Contents (each function cites the part of the paper it follows):
 * ``hyb_ell_width`` -- the ELL width rule used for the HYB format.
 * ``mlp_forward``   -- the selector's 2-layer MLP (Section 5.4 relies on
                        multi-class classification; this is its forward pass).
+* ``time_head``, ``conversion_cost_us``, ``gate``
+                    -- the run-time mode's decision (Section 5.3 steps 3-4):
+                       predicted product times, predicted conversion cost,
+                       and the convert-only-if-it-pays rule.
 * ``cg``            -- conjugate gradients (Hestenes-Stiefel) with its
                        products from ``spmv_coo``: the iterative solver whose
                        repeated SpMV amortises selection and conversion
@@ -279,6 +283,44 @@ def mlp_forward(fvec, mu, sigma, W1, b1, W2, b2) -> np.ndarray:
     z = mlp_inputs(fvec, mu, sigma)
     h = np.maximum(np.asarray(W1, np.float64) @ z + np.asarray(b1, np.float64), 0.0)
     return np.asarray(W2, np.float64) @ h + np.asarray(b2, np.float64)
+
+
+# ---------------------------------------------------------------------------
+# Run-time mode decision (Section 5.3, steps 3-4; overheads in Section 7.5)
+# ---------------------------------------------------------------------------
+
+def time_head(fvec, mu, sigma, W1, b1, W3, b3) -> np.ndarray:
+    """Predicted natural log of microseconds per product: W3 relu(W1 z + b1)
+    + b3 on the same hidden layer as ``mlp_forward``.
+
+    One output per label class, then one for default CSR (the configuration
+    a fresh matrix runs in).  This is the regression counterpart of the
+    classifier that Section 5.3 uses to weigh the gain of a new format
+    against the optimisation overhead.  W3 is (K+1) x H."""
+    z = mlp_inputs(fvec, mu, sigma)
+    h = np.maximum(np.asarray(W1, np.float64) @ z + np.asarray(b1, np.float64), 0.0)
+    return np.asarray(W3, np.float64) @ h + np.asarray(b3, np.float64)
+
+
+def conversion_cost_us(coef, nnz: int, m: int) -> float:
+    """Predicted time of converting to one format (Section 5.3 step 3, the
+    c_latency of Section 7.5): the linear model a + b*nnz + c*m in
+    microseconds, clamped below at zero.  ``coef`` = (a, b, c)."""
+    a, b, c = (float(v) for v in coef)
+    return max(0.0, a + b * float(nnz) + c * float(m))
+
+
+def gate(t_current_us: float, t_selected_us: float, select_us: float,
+         pack_us: float, expected_runs: int) -> bool:
+    """Section 5.3 step 4: convert only when the predicted benefit over the
+    expected number of products is larger than the overhead.
+
+    benefit  = (t_current - t_selected) * expected_runs
+    overhead = select_us (feature extraction + prediction, f_latency +
+               o_latency + p_latency of Section 7.5) + pack_us (c_latency)
+    Returns True to convert; a tie keeps the current format."""
+    benefit = (float(t_current_us) - float(t_selected_us)) * float(expected_runs)
+    return benefit > float(select_us) + float(pack_us)
 
 
 # ---------------------------------------------------------------------------

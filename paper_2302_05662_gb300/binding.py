@@ -32,7 +32,8 @@ EXPORTED = ("spmv_config_default", "spmv_create", "spmv_set_config", "spmv_get_c
             "spmv_last_error", "spmv_coo_run_noalloc", "spmv_features", "spmv_selector_load",
             "spmv_selector_infer", "spmv_select", "spmv_batch_create", "spmv_batch_tune",
             "spmv_batch_launch", "spmv_batch_get_plan", "spmv_batch_destroy", "spmv_batch_run",
-            "spmv_select_runtime", "spmv_cg", "spmv_set_panel_limit", "spmv_get_panel_limit")
+            "spmv_select_runtime", "spmv_cg", "spmv_set_panel_limit", "spmv_get_panel_limit",
+            "spmv_probe_gather_floor", "spmv_probe_fp64_fma")
 
 
 class SpmvError(RuntimeError):
@@ -129,6 +130,8 @@ def load_library(path: str | None = None):
         "spmv_cg": (ctypes.c_int, [_VP, _VP, _VP, _D, _I32, _VP, ctypes.POINTER(spmv_cg_result), _VP]),
         "spmv_set_panel_limit": (ctypes.c_int, [_I64]),
         "spmv_get_panel_limit": (_I64, []),
+        "spmv_probe_gather_floor": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+        "spmv_probe_fp64_fma": (ctypes.c_int, [_I64, _VP, ctypes.POINTER(_I64), _VP]),
         "spmv_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -429,6 +432,27 @@ def spmv_coo_run_noalloc(m: int, n: int, rows, cols, vals, alpha: float, x, beta
     _check(load_library().spmv_coo_run_noalloc(int(m), int(n), nnz, rp, cp, vp, vt, float(alpha),
                                                _vec(x, int(n), vt, "x"), float(beta),
                                                _vec(y, int(m), vt, "y"), _stream(stream)))
+
+
+def spmv_probe_gather_floor(h: int, x, y, stream=None):
+    """Measurement kernel (include/spmv_probe.h): the handle's bytes moved
+    with ideal access and its x gathers, no floating-point arithmetic; y
+    receives meaningless bits."""
+    m, n, vt = _shape(h)
+    _check(load_library().spmv_probe_gather_floor(h, _vec(x, n, vt, "x"), _vec(y, m, vt, "y"),
+                                                  _stream(stream)))
+
+
+def spmv_probe_fp64_fma(iterations: int, sink, stream=None) -> int:
+    """Measurement kernel: a full wave of independent fp64 FMA chains.
+    Returns the number of fused multiply-adds launched (2 flops each)."""
+    import torch
+    if sink.dtype != torch.float64 or sink.numel() < 1:
+        raise SpmvError(SPMV_ERR_INVALID, "sink: one float64 entry needed")
+    count = _I64(0)
+    _check(load_library().spmv_probe_fp64_fma(int(iterations), _ptr(sink), ctypes.byref(count),
+                                              _stream(stream)))
+    return int(count.value)
 
 
 def spmv_destroy(h: int):

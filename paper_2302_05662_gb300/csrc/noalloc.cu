@@ -52,7 +52,10 @@ std::mutex g_na_mu;
 void *g_na_addr[256] = {};
 
 // Device address of the scratch on the current device, looked up once per
-// device (the first call on a device does this set-up).
+// device (the first call on a device does this set-up).  The address is kept
+// for the life of the process: cudaDeviceReset on a device destroys the
+// context that holds the array, so the entry point must not be used on a
+// device after it has been reset.
 int scratch_address(unsigned char **out) {
     int dev = 0;
     SPMV_CUDA_TRY(cudaGetDevice(&dev));
@@ -186,12 +189,27 @@ extern "C" int spmv_coo_run_noalloc(int64_t m, int64_t n, int64_t nnz, const int
         set_error("spmv_coo_run_noalloc: nonzeros in an empty matrix");
         return SPMV_ERR_INVALID;
     }
+    // the kernel reads whole chunks with 16-byte vector loads from the
+    // caller's arrays, so their base addresses must be 16-byte aligned (a
+    // view starting mid-array is refused here, before anything is launched)
+    if (nnz > 0 && (((uintptr_t)d_rows | (uintptr_t)d_cols | (uintptr_t)d_vals) & 15u) != 0) {
+        set_error("spmv_coo_run_noalloc: d_rows, d_cols and d_vals must be 16-byte aligned");
+        return SPMV_ERR_INVALID;
+    }
     if (m == 0) return SPMV_OK;
     if (!d_y) {
         set_error("spmv_coo_run_noalloc: NULL y");
         return SPMV_ERR_INVALID;
     }
     cudaStream_t s = (cudaStream_t)stream;
+    // every call with nonzeros waits on the stream to read its triplet
+    // check, which a stream being captured into a graph does not allow
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    SPMV_CUDA_TRY(cudaStreamIsCapturing(s, &cap));
+    if (cap != cudaStreamCaptureStatusNone) {
+        set_error("spmv_coo_run_noalloc: the stream is being captured; this call synchronises it");
+        return SPMV_ERR_UNSUPPORTED;
+    }
     switch (value_type) {
     case SPMV_F64: return run_noalloc<SPMV_F64>(m, n, nnz, d_rows, d_cols, d_vals, alpha, d_x, beta, d_y, s);
     case SPMV_F32: return run_noalloc<SPMV_F32>(m, n, nnz, d_rows, d_cols, d_vals, alpha, d_x, beta, d_y, s);
