@@ -52,15 +52,20 @@ typedef enum {
     SPMV_ERR_OOM = -2,         /* device allocation failed                 */
     SPMV_ERR_CUDA = -3,        /* a CUDA runtime call failed               */
     SPMV_ERR_UNSUPPORTED = -4, /* valid but not supported (e.g. ELL width) */
-    SPMV_ERR_BOUNDS = -5,      /* reserved: no entry point returns it       */
-    SPMV_ERR_TIMEOUT = -6      /* reserved: no kernel waits on another      */
+    SPMV_ERR_BOUNDS = -5,      /* a checked kernel skipped an out-of-range
+                                  index (spmv_check)                       */
+    SPMV_ERR_TIMEOUT = -6      /* a kernel gave up waiting for a copy
+                                  (spmv_check)                             */
 } spmv_status;
 /* Out-of-range triplets are found by a device check in spmv_create and
- * reported as SPMV_ERR_INVALID.  No kernel spins on a flag: rows shared by
- * work units are joined by whichever unit arrives last, the batched kernel
- * takes work from one atomic counter, and conjugate gradients stop through
- * a graph conditional node; so no call can wait on the device without
- * bound, and the last two codes are kept only for ABI stability. */
+ * reported as SPMV_ERR_INVALID.  No kernel spins on another work unit: rows
+ * shared by work units are joined by whichever unit arrives last, the
+ * batched kernel takes work from one atomic counter, and conjugate
+ * gradients stop through a graph conditional node.  The one wait on the
+ * device is for the copy engine: the staged CSR kernel waits on a shared-
+ * memory barrier for each bulk copy, for at most one second, after which it
+ * records a timeout in the handle's device status word and returns; the
+ * asynchronous spmv_run cannot report it, spmv_check does. */
 
 typedef enum { SPMV_F64 = 0, SPMV_F32 = 1, SPMV_BF16 = 2 } spmv_dtype;
 
@@ -74,7 +79,10 @@ typedef enum {
                       /* descending length (Sec. 2.3 SELL)                 */
 } spmv_format;
 
-/* threads_per_row value that selects the nnz-balanced CSR kernel. */
+/* threads_per_row value that selects the nnz-balanced CSR kernel: tiles of
+ * a fixed number of nonzeros, each bulk-copied into shared memory while the
+ * thread block multiplies the previous one, rows summed by groups of lanes
+ * (1..8 from the mean row length) and joined across tiles. */
 #define SPMV_TPR_SPLIT (-1)
 
 /*
@@ -106,7 +114,10 @@ typedef enum {
  *                     k such that at least max(4096, m/3) rows hold k or
  *                     more nonzeros).  SELL: columns of a slice per work
  *                     item, 8..65536 (0 = 128); wider slices are split into
- *                     several items joined in order.
+ *                     several items joined in order.  CSR with
+ *                     SPMV_TPR_SPLIT: nonzeros per tile staged through
+ *                     shared memory, a multiple of 256 in [256, 8192]
+ *                     (0 = 4096).
  * spmv_config_default() fills the defaults (carveout = -1; unroll and
  * regcap 0, resolved per format and value type when the configuration is
  * applied; spmv_get_config returns the resolved values).
@@ -471,6 +482,18 @@ SPMV_API int spmv_cg(spmv_handle h, const void *d_b, void *d_x, double tol,
 #define SPMV_PANEL_LIMIT_MAX 2146435072LL
 SPMV_API int spmv_set_panel_limit(int64_t max_triplets);
 SPMV_API int64_t spmv_get_panel_limit(void);
+
+/*
+ * Reads and clears the handle's device status word (no counterpart in the
+ * paper).  Kernels launched by spmv_run cannot return a status to the host,
+ * so a kernel that gives up waiting for a bulk copy (one second; the staged
+ * CSR kernel) records it in a word on the device, as does a kernel that
+ * finds and skips an out-of-range index.  spmv_check synchronises `stream`,
+ * then returns SPMV_ERR_BOUNDS or SPMV_ERR_TIMEOUT if any product since the
+ * last check recorded one (the products concerned are incomplete), else
+ * SPMV_OK.  Errors: SPMV_ERR_INVALID (NULL handle), SPMV_ERR_CUDA.
+ */
+SPMV_API int spmv_check(spmv_handle h, void *stream);
 
 /* Frees every device array of the handle.  NULL is accepted. */
 SPMV_API int spmv_destroy(spmv_handle h);

@@ -33,7 +33,7 @@ EXPORTED = ("spmv_config_default", "spmv_create", "spmv_set_config", "spmv_get_c
             "spmv_selector_infer", "spmv_select", "spmv_batch_create", "spmv_batch_tune",
             "spmv_batch_launch", "spmv_batch_get_plan", "spmv_batch_destroy", "spmv_batch_run",
             "spmv_select_runtime", "spmv_cg", "spmv_set_panel_limit", "spmv_get_panel_limit",
-            "spmv_probe_gather_floor", "spmv_probe_fp64_fma")
+            "spmv_probe_gather_floor", "spmv_probe_fp64_fma", "spmv_check")
 
 
 class SpmvError(RuntimeError):
@@ -131,6 +131,7 @@ def load_library(path: str | None = None):
         "spmv_set_panel_limit": (ctypes.c_int, [_I64]),
         "spmv_get_panel_limit": (_I64, []),
         "spmv_probe_gather_floor": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+        "spmv_check": (ctypes.c_int, [_VP, _VP]),
         "spmv_probe_fp64_fma": (ctypes.c_int, [_I64, _VP, ctypes.POINTER(_I64), _VP]),
         "spmv_last_error": (ctypes.c_char_p, []),
     }
@@ -432,6 +433,12 @@ def spmv_coo_run_noalloc(m: int, n: int, rows, cols, vals, alpha: float, x, beta
     _check(load_library().spmv_coo_run_noalloc(int(m), int(n), nnz, rp, cp, vp, vt, float(alpha),
                                                _vec(x, int(n), vt, "x"), float(beta),
                                                _vec(y, int(m), vt, "y"), _stream(stream)))
+
+
+def spmv_check(h: int, stream=None):
+    """Raise SpmvError if a product since the last check recorded a device
+    error (a copy wait that timed out, a skipped out-of-range index)."""
+    _check(load_library().spmv_check(h, _stream(stream)))
 
 
 def spmv_probe_gather_floor(h: int, x, y, stream=None):

@@ -8,6 +8,7 @@
 #include <mutex>
 #include <utility>
 
+#include "bulk.cuh"
 #include "internal.cuh"
 
 namespace spmv {
@@ -161,6 +162,13 @@ int resolve_config(const spmv_matrix *h, const spmv_config *in, spmv_config *out
             set_error("config: CSR threads_per_row %d not in {1..32 powers of two, -1}", c.threads_per_row);
             return SPMV_ERR_INVALID;
         }
+        if (c.threads_per_row == SPMV_TPR_SPLIT) {  // nonzeros per staged tile
+            if (c.hyb_ell_width == 0) c.hyb_ell_width = 4096;
+            if (c.hyb_ell_width < 256 || c.hyb_ell_width > 8192 || c.hyb_ell_width % 256 != 0) {
+                set_error("config: CSR tile size %d not a multiple of 256 in [256, 8192]", c.hyb_ell_width);
+                return SPMV_ERR_INVALID;
+            }
+        }
         break;
     case SPMV_FMT_BSR:
         if (c.threads_per_row == 0) c.threads_per_row = 1;
@@ -202,6 +210,8 @@ void destroy_all(spmv_matrix *h) {
     h->panel_row0 = nullptr;
     h->npanels = 0;
     free_packed(h);
+    if (h->d_status) cudaFree(h->d_status);
+    h->d_status = nullptr;
     if (h->rowptr) cudaFree(h->rowptr);
     if (h->colidx) cudaFree(h->colidx);
     if (h->vals) cudaFree(h->vals);
@@ -368,8 +378,11 @@ int spmv_create(spmv_handle *out, int64_t m, int64_t n, int64_t nnz, const int32
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&h->d_status), sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) {
         int st = cuda_status(e, "device query");
+        if (h->d_status) cudaFree(h->d_status);
         delete h;
         return st;
     }
@@ -606,6 +619,36 @@ int spmv_export(spmv_handle h, int32_t array_id, void *d_dst, int64_t bytes, voi
     if (array_id == SPMV_ARR_ELL_COLIDX && h->ell_d16)  // 16-bit row offsets: export int32 columns
         return decode_ell_columns(h, static_cast<int32_t *>(d_dst), (cudaStream_t)stream);
     SPMV_CUDA_TRY(cudaMemcpyAsync(d_dst, p, (size_t)have, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return SPMV_OK;
+}
+
+int spmv_check(spmv_handle h, void *stream) {
+    g_err[0] = 0;
+    if (!h) {
+        set_error("spmv_check: NULL handle");
+        return SPMV_ERR_INVALID;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned bits = 0;
+    const int parts = h->npanels > 0 ? h->npanels : 1;
+    for (int p = 0; p < parts; ++p) {
+        spmv_matrix *q = h->npanels > 0 ? h->panels[p] : h;
+        if (!q->d_status) continue;
+        unsigned w = 0;
+        SPMV_CUDA_TRY(cudaMemcpyAsync(&w, q->d_status, sizeof w, cudaMemcpyDeviceToHost, s));
+        SPMV_CUDA_TRY(cudaStreamSynchronize(s));
+        if (w) SPMV_CUDA_TRY(cudaMemsetAsync(q->d_status, 0, sizeof w, s));
+        bits |= w;
+    }
+    SPMV_CUDA_TRY(cudaStreamSynchronize(s));
+    if (bits & STATUS_BOUNDS) {
+        set_error("spmv_check: a kernel found an index out of bounds and skipped the access");
+        return SPMV_ERR_BOUNDS;
+    }
+    if (bits & STATUS_TIMEOUT) {
+        set_error("spmv_check: a kernel gave up waiting for a copy; its product is incomplete");
+        return SPMV_ERR_TIMEOUT;
+    }
     return SPMV_OK;
 }
 

@@ -848,11 +848,17 @@ int gather_panel(const int32_t *d_rows, const int32_t *d_cols, const void *d_val
     return SPMV_OK;
 }
 
+// The CSR arrays are allocated CSR_PAD entries longer than needed: the
+// staged tile kernel copies whole multiples of 8 column/value entries and
+// 16-byte windows of row pointers, so the last tile may read up to 7 entries
+// past nnz and 3 past m (never used).
+constexpr size_t CSR_PAD = 8;
+
 int build_csr(spmv_matrix *h, const int32_t *d_rows, const int32_t *d_cols, const void *d_vals,
               cudaStream_t s) {
     const int64_t m = h->m, n = h->n, nnz_in = h->nnz;
     const size_t vs = value_size(h->vt);
-    SPMV_TRY(dalloc(&h->rowptr, (size_t)m + 1));
+    SPMV_TRY(dalloc(&h->rowptr, (size_t)m + 1 + CSR_PAD));  // staged windows may read 3 past m
     if (nnz_in == 0) {
         SPMV_CUDA_TRY(cudaMemsetAsync(h->rowptr, 0, sizeof(int) * (m + 1), s));
         SPMV_TRY(dalloc(&h->colidx, 1));
@@ -877,8 +883,8 @@ int build_csr(spmv_matrix *h, const int32_t *d_rows, const int32_t *d_cols, cons
     if (!(hflags & 6u)) {
         // already sorted by (row, col) with no repeated pair: copy and index
         h->nnz = nnz_in;
-        SPMV_TRY(dalloc(&h->colidx, (size_t)nnz_in));
-        SPMV_TRY(dalloc_bytes(&h->vals, vs * nnz_in));
+        SPMV_TRY(dalloc(&h->colidx, (size_t)nnz_in + CSR_PAD));
+        SPMV_TRY(dalloc_bytes(&h->vals, vs * (nnz_in + CSR_PAD)));
         SPMV_CUDA_TRY(cudaMemcpyAsync(h->colidx, d_cols, sizeof(int) * nnz_in, cudaMemcpyDeviceToDevice, s));
         SPMV_CUDA_TRY(cudaMemcpyAsync(h->vals, d_vals, vs * nnz_in, cudaMemcpyDeviceToDevice, s));
         k_rowptr_from_sorted<<<grid1d(m + 1, 256), 256, 0, s>>>(d_rows, nnz_in, m, h->rowptr);
@@ -904,8 +910,8 @@ int build_csr(spmv_matrix *h, const int32_t *d_rows, const int32_t *d_cols, cons
         SPMV_TRY(exclusive_scan(head.p, pos.p, nnz_in, s, &nu));
         h->nnz = nu;
         SPMV_TRY(urows.alloc(nu, s));
-        SPMV_TRY(dalloc(&h->colidx, (size_t)nu));
-        SPMV_TRY(dalloc_bytes(&h->vals, vs * nu));
+        SPMV_TRY(dalloc(&h->colidx, (size_t)nu + CSR_PAD));
+        SPMV_TRY(dalloc_bytes(&h->vals, vs * (nu + CSR_PAD)));
         if (h->vt == SPMV_F64)
             merge_dispatch<double>(ks, vp, d_vals, head.p, pos.p, nnz_in, colbits, urows.p, h->colidx, h->vals, s);
         else if (h->vt == SPMV_F32)
@@ -1324,7 +1330,8 @@ int pack_format(spmv_matrix *h, const spmv_config &cfg, cudaStream_t s) {
     switch (cfg.format) {
     case SPMV_FMT_CSR:
         if (cfg.threads_per_row == SPMV_TPR_SPLIT) {
-            SPMV_TRY(ensure_seg_scratch(h, items, true, s));
+            // nonzero tiles: hyb_ell_width = nonzeros per tile (a multiple of 256)
+            SPMV_TRY(ensure_seg_scratch(h, cfg.hyb_ell_width / 32, true, s));
         } else {
             // rows needing more than 32 steps of their lane group go to whole blocks
             const int64_t thr = std::max<int64_t>(512, 32LL * cfg.threads_per_row * cfg.unroll);

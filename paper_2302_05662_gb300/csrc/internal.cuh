@@ -289,6 +289,9 @@ struct spmv_matrix {
     spmv::LongRows lng;
     // conjugate-gradient plan (cg.cu): scratch vectors and the solve's graph
     spmv::CgPlan *cg = nullptr;
+    // device status word: kernels that wait on a copy record a timeout here
+    // (bits STATUS_TIMEOUT, STATUS_BOUNDS); spmv_check reads and clears it
+    unsigned *d_status = nullptr;
     // row panels: a matrix with more triplets than one handle indexes with
     // int32 offsets is held as sub-handles over rows [panel_row0[p],
     // panel_row0[p+1]); the parent then holds no arrays of its own

@@ -15,6 +15,7 @@
 
 #include <climits>
 
+#include "bulk.cuh"
 #include "combine.cuh"
 
 namespace spmv {
@@ -266,6 +267,207 @@ __device__ __forceinline__ void csr_split_chunk(int64_t c, int64_t nnz, int64_t 
             const int64_t c0 = s0 / C, c1 = (next_end - 1) / C;
             seg_arrive<T, false>(cur, c, c0, c1, sc, P, y, ep);
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Nonzero tiles staged through shared memory (the nnz-balanced CSR kernel).
+// Tile t holds the nonzeros [t TILE, (t+1) TILE); a thread block takes tiles
+// t = blockIdx.x, + gridDim.x, ..., with two shared-memory stages: while it
+// multiplies one tile, the copy engine brings the block's next tile (column
+// indices and values, one bulk copy each) into the other stage.  Inside a
+// tile, groups of TPR lanes take the tile's rows, each lane summing a strided
+// part of its row from shared memory with one fused multiply-add per entry
+// (UNROLL x gathers in flight) and the group adding its lanes' sums -- the
+// row-sequential accumulation that keeps fp64 instructions at one per
+// nonzero, with the loads of the row-major CSR arrays made contiguous by the
+// bulk copies.  A row cut by a tile boundary is joined in tile order through
+// the partials; a row segment longer than `long_len` is summed by the whole
+// block after the groups finish.  meta0[t] = row holding entry t TILE,
+// meta0[ntiles] = m - 1.  The column and value arrays must be readable up to
+// the next multiple of 8 entries past nnz (their allocations are padded).
+// ---------------------------------------------------------------------------
+struct TileSmem {
+    int stage_bytes, cols_off, vals_off, rows_off, hdr_off, bar_off, list_off, red_off, total;
+};
+
+// Rows of a tile whose row pointers are staged with it: at most TILE_ROWS + 1
+// pointers (a tile with more rows, i.e. many empty rows, reads them from
+// global memory instead).
+constexpr int TILE_ROWS = 1024;
+
+template <typename V>
+__host__ __device__ inline TileSmem tile_smem_layout(int tile, int long_max) {
+    TileSmem L;
+    const int cb = (tile * 4 + 127) / 128 * 128;
+    const int vb = (tile * (int)sizeof(V) + 127) / 128 * 128;
+    const int rb = ((TILE_ROWS + 8) * 4 + 127) / 128 * 128;
+    L.cols_off = 0;
+    L.vals_off = cb;
+    L.rows_off = cb + vb;
+    L.hdr_off = cb + vb + rb;                      // per stage: first row, last row, window base, staged
+    L.stage_bytes = L.hdr_off + 128;
+    L.bar_off = 2 * L.stage_bytes;                 // two stages, then 2 mbarriers
+    L.list_off = L.bar_off + 16;                   // long segments: int4 (row, begin, end, -) + count
+    L.red_off = L.list_off + 16 * long_max + 16;   // block reduction scratch: 32 doubles
+    L.total = L.red_off + 32 * 8;
+    return L;
+}
+
+template <typename V, typename T, int TPR, int UNROLL>
+__global__ void __launch_bounds__(1024)
+k_csr_tiles(int64_t nnz, int64_t m, int64_t ntiles, int tile, int long_len, int long_max,
+            const int *__restrict__ rowptr, const int *__restrict__ cols, const V *__restrict__ vals,
+            const T *__restrict__ x, T *__restrict__ y, T alpha, T beta, const int *__restrict__ meta0,
+            const PartialsT<T> P, unsigned *status) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const TileSmem L = tile_smem_layout<V>(tile, long_max);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar_off);
+    int4 *list = reinterpret_cast<int4 *>(smem + L.list_off);
+    int *nlist = reinterpret_cast<int *>(smem + L.list_off + 16 * long_max);
+    T *red = reinterpret_cast<T *>(smem + L.red_off);
+    const Epi<T> ep(alpha, beta);
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int G = blockDim.x / TPR, g = tid / TPR, sub = tid % TPR;
+    const unsigned gmask = TPR == 32 ? 0xffffffffu : (((1u << TPR) - 1u) << (lane / TPR * TPR));
+
+    // tile t's first and last rows (meta0 holds the row of entry t*tile)
+    auto first_row = [&](int64_t t) -> int { return t == 0 ? 0 : __ldg(meta0 + t); };
+    // one thread issues the copies of tile t (rows rb..re) into a stage: the
+    // column indices and values of its nonzeros, the row pointers of its
+    // rows (16-byte aligned window) when they fit, and a header the
+    // barrier's completion publishes with them
+    auto issue = [&](int64_t t, int st, int rb, int re) {
+        const int64_t e0 = t * tile;
+        const int64_t cnt = (e0 + tile < nnz ? tile : nnz - e0);
+        const unsigned n8 = (unsigned)((cnt + 7) & ~int64_t(7));
+        unsigned char *base = smem + st * L.stage_bytes;
+        const int w0 = rb & ~3;
+        const unsigned nw = (unsigned)((re + 2 - w0 + 3) & ~3);
+        const bool staged = nw <= (unsigned)(TILE_ROWS + 8);
+        int *hdr = reinterpret_cast<int *>(base + L.hdr_off);
+        hdr[0] = rb;
+        hdr[1] = re;
+        hdr[2] = w0;
+        hdr[3] = staged;
+        const unsigned bytes = n8 * 4u + n8 * (unsigned)sizeof(V) + (staged ? nw * 4u : 0u);
+        mbar_arrive_expect_tx(bar + st, bytes);
+        bulk_copy_g2s(base + L.cols_off, cols + e0, n8 * 4u, bar + st);
+        bulk_copy_g2s(base + L.vals_off, vals + e0, n8 * (unsigned)sizeof(V), bar + st);
+        if (staged) bulk_copy_g2s(base + L.rows_off, rowptr + w0, nw * 4u, bar + st);
+    };
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        mbar_init(bar + 1, 1);
+        *nlist = 0;
+        mbar_init_fence();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int i = 0; i < 2; ++i) {
+            const int64_t t = blockIdx.x + (int64_t)i * gridDim.x;
+            if (t < ntiles) issue(t, i, first_row(t), __ldg(meta0 + t + 1));
+        }
+    }
+    int k = 0;  // tiles this block has taken
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+        const int st = k & 1;
+        // rows of the block's tile after next, fetched now, used when its
+        // copies are issued at the end of this tile
+        const int64_t tn = t + 2 * (int64_t)gridDim.x;
+        int nrb = 0, nre = 0;
+        if (tid == 0 && tn < ntiles) {
+            nrb = first_row(tn);
+            nre = __ldg(meta0 + tn + 1);
+        }
+        const bool ok = mbar_wait_bounded(bar + st, (unsigned)(k >> 1) & 1u, MBAR_WAIT_NS);
+        if (__syncthreads_or(!ok)) {
+            // a copy did not complete in time: record it, let the copies
+            // already issued finish (bounded), and stop
+            if (tid == 0) {
+                atomicOr(status, STATUS_TIMEOUT);
+                mbar_wait_bounded(bar + (st ^ 1), (unsigned)((k + 1) >> 1) & 1u, MBAR_WAIT_NS);
+            }
+            return;
+        }
+        const unsigned char *base = smem + st * L.stage_bytes;
+        const int *sc = reinterpret_cast<const int *>(base + L.cols_off);
+        const V *sv = reinterpret_cast<const V *>(base + L.vals_off);
+        const int *srp = reinterpret_cast<const int *>(base + L.rows_off);
+        const int *hdr = reinterpret_cast<const int *>(base + L.hdr_off);
+        const int rb = hdr[0], re = hdr[1], wbase = hdr[2];
+        const bool staged = hdr[3] != 0;
+        auto rp = [&](int r) -> int { return staged ? srp[r - wbase] : __ldg(rowptr + r); };
+        const int64_t E0 = t * tile, E1 = E0 + tile < nnz ? E0 + tile : nnz;
+        for (int r = rb + g; r <= re; r += G) {
+            const int rs = rp(r), rend = rp(r + 1);
+            if (rs == rend) {  // empty row: written by the one tile whose range ends at or after it
+                if (sub == 0 && ((rs > E0 && rs <= E1) || (rs == 0 && t == 0))) ep.store(y, r, T(0));
+                continue;
+            }
+            const int s = rs > E0 ? rs : (int)E0, e = rend < E1 ? rend : (int)E1;
+            if (s >= e) continue;
+            if (e - s > long_len) {  // left to the whole block below
+                if (sub == 0) {
+                    const int i = atomicAdd(nlist, 1);
+                    if (i < long_max) list[i] = make_int4(r, s, e, 0);
+                }
+                continue;
+            }
+            T acc = T(0);
+            for (int q = s + sub; q < e; q += TPR * UNROLL) {
+                int c[UNROLL];
+                T v[UNROLL], xv[UNROLL];
+#pragma unroll
+                for (int u = 0; u < UNROLL; ++u) {
+                    const int qq = q + u * TPR;
+                    c[u] = qq < e ? sc[qq - E0] : -1;
+                    v[u] = qq < e ? (T)sv[qq - E0] : T(0);
+                }
+#pragma unroll
+                for (int u = 0; u < UNROLL; ++u) xv[u] = c[u] >= 0 ? ld_x(x, c[u]) : T(0);
+#pragma unroll
+                for (int u = 0; u < UNROLL; ++u)
+                    if (c[u] >= 0) acc = fma(v[u], xv[u], acc);
+            }
+#pragma unroll
+            for (int off = TPR / 2; off > 0; off >>= 1) acc += __shfl_down_sync(gmask, acc, off, TPR);
+            if (sub == 0) {
+                T total = acc;
+                if (rs >= E0 && rend <= E1) ep.store(y, r, total);
+                else if (join_partial<T>(t, rs / tile, (rend - 1) / tile, 0, acc, P, &total)) ep.store(y, r, total);
+            }
+        }
+        __syncthreads();
+        const int nl = *nlist < long_max ? *nlist : long_max;
+        for (int i = 0; i < nl; ++i) {  // long row segments: every thread strides, then a block sum
+            const int4 d = list[i];
+            T acc = T(0);
+            for (int q = d.y + tid; q < d.z; q += blockDim.x) acc = fma((T)sv[q - E0], ld_x(x, sc[q - E0]), acc);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+            if (lane == 0) red[tid >> 5] = acc;
+            __syncthreads();
+            if (tid == 0) {
+                T sum = T(0);
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += red[w];
+                const int rs = rp(d.x), rend = rp(d.x + 1);
+                T total = sum;
+                if (rs >= E0 && rend <= E1) ep.store(y, d.x, total);
+                else if (join_partial<T>(t, rs / tile, (rend - 1) / tile, 0, sum, P, &total))
+                    ep.store(y, d.x, total);
+            }
+            __syncthreads();
+        }
+        // stage st is free: the block's tile after next goes into it
+        if (tid == 0) {
+            *nlist = 0;
+            if (tn < ntiles) {
+                fence_proxy_async_smem();
+                issue(tn, st, nrb, nre);
+            }
+        }
+        __syncthreads();
     }
 }
 

@@ -3,6 +3,7 @@
 // the ~150 kernel variants compile in parallel.
 #pragma once
 
+#include <algorithm>
 #include <type_traits>
 
 #include "kernels_rows.cuh"
@@ -262,18 +263,48 @@ int run_hyb_vt(const spmv_matrix *h, double alpha, const void *x, double beta, v
                                  (const T *)x, (T)beta, (T *)y, s);
 }
 
-template <typename V, typename T, int ITEMS>
-int launch_split(const spmv_matrix *h, T alpha, const T *x, T beta, T *y, cudaStream_t s) {
-    auto kern = k_csr_split<V, T, ITEMS>;
-    const int tpb = ITEMS >= 16 && h->cfg.threads_per_block > 512 ? 512 : h->cfg.threads_per_block;
+// occupancy-limited resident blocks per SM with dynamic shared memory (not cached)
+inline int resident_blocks_smem(const void *kernel, int threads, size_t smem) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem) != cudaSuccess || nb < 1) {
+        cudaGetLastError();
+        nb = 1;
+    }
+    return nb;
+}
+
+// the staged nonzero-tile kernel: lanes per row from the mean row length (at
+// most 8), gathers in flight per lane 4 (unroll <= 2) or 8 (unroll 4)
+template <typename V, typename T, int TPR, int U>
+int launch_tiles(const spmv_matrix *h, T alpha, const T *x, T beta, T *y, cudaStream_t s) {
+    auto kern = k_csr_tiles<V, T, TPR, U>;
+    const int tpb = h->cfg.threads_per_block < TPR ? TPR : h->cfg.threads_per_block;
+    const int tile = 32 * h->seg.items;
+    // a row segment longer than 8 gathers per lane goes to the whole block
+    const int long_len = std::max(32, 8 * TPR * U);
+    const int long_max = tile / long_len + 2;
+    const TileSmem L = tile_smem_layout<V>(tile, long_max);
+    SPMV_CUDA_TRY(cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total));
     SPMV_TRY(apply_carveout((const void *)kern, h->cfg.carveout));
-    const int64_t chunks = (h->nnz + 32 * ITEMS - 1) / (32 * ITEMS);
-    const int64_t wpb = tpb / 32;
-    const int grid = wave_grid((const void *)kern, tpb, (chunks + wpb - 1) / wpb, h->sm_count);
-    kern<<<grid, tpb, 0, s>>>(h->nnz, h->m, h->rowptr, h->colidx, (const V *)h->vals, x, y, alpha, beta,
-                              h->seg.meta0, PartialsT<T>::of(h->seg.part));
+    const int64_t ntiles = h->seg.nchunks;
+    const int64_t cap = (int64_t)resident_blocks_smem((const void *)kern, tpb, L.total) * h->sm_count;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, cap));
+    kern<<<grid, tpb, L.total, s>>>(h->nnz, h->m, ntiles, tile, long_len, long_max, h->rowptr, h->colidx,
+                                    (const V *)h->vals, x, y, alpha, beta, h->seg.meta0,
+                                    PartialsT<T>::of(h->seg.part), h->d_status);
     SPMV_LAUNCH_CHECK();
     return SPMV_OK;
+}
+
+template <typename V, typename T, int U>
+int tiles_tpr(const spmv_matrix *h, T a, const T *x, T b, T *y, cudaStream_t s) {
+    const int tpr = std::min(8, default_tpr(h));
+    switch (tpr) {
+    case 1: return launch_tiles<V, T, 1, U>(h, a, x, b, y, s);
+    case 2: return launch_tiles<V, T, 2, U>(h, a, x, b, y, s);
+    case 4: return launch_tiles<V, T, 4, U>(h, a, x, b, y, s);
+    default: return launch_tiles<V, T, 8, U>(h, a, x, b, y, s);
+    }
 }
 
 template <int VT>
@@ -281,11 +312,8 @@ int run_csr_split_vt(const spmv_matrix *h, double alpha, const void *x, double b
     using V = typename VT_<VT>::V;
     using T = typename VT_<VT>::T;
     const T a = (T)alpha, b = (T)beta;
-    switch (h->seg.items) {
-    case 4: return launch_split<V, T, 4>(h, a, (const T *)x, b, (T *)y, s);
-    case 8: return launch_split<V, T, 8>(h, a, (const T *)x, b, (T *)y, s);
-    default: return launch_split<V, T, 16>(h, a, (const T *)x, b, (T *)y, s);
-    }
+    if (h->cfg.unroll >= 4) return tiles_tpr<V, T, 8>(h, a, (const T *)x, b, (T *)y, s);
+    return tiles_tpr<V, T, 4>(h, a, (const T *)x, b, (T *)y, s);
 }
 
 template <int VT>
