@@ -28,6 +28,11 @@
  *     accumulate in float.  Indices are int32 (m, n < 2^31, nnz < 2^31).
  *   - A handle is not thread-safe; runs on one handle must be ordered on
  *     one stream (they share the handle's reduction scratch).
+ *   - Fault injection (for testing callers' error paths): with the
+ *     environment variable SPMV_FAULT_ALLOC=k (k >= 1), the k-th device
+ *     allocation made inside each call fails as if the device were out of
+ *     memory; the call returns SPMV_ERR_OOM after releasing what it had
+ *     allocated.  Unset (the default), nothing is injected.
  */
 #ifndef SPMV_GB300_SPMV_H
 #define SPMV_GB300_SPMV_H

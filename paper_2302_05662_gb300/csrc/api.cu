@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -15,6 +16,38 @@ namespace spmv {
 
 namespace {
 thread_local char g_err[512] = "";
+thread_local long long g_alloc_count = 0;
+
+// SPMV_FAULT_ALLOC=k (k >= 1): the k-th allocation of each entry-point call
+// fails; read on every allocation so a test can set and clear it at will
+bool fault_injected() {
+    const char *v = std::getenv("SPMV_FAULT_ALLOC");
+    ++g_alloc_count;
+    if (!v || !*v) return false;
+    const long long k = std::atoll(v);
+    return k > 0 && g_alloc_count == k;
+}
+}  // namespace
+
+void entry_reset() {
+    entry_reset();
+    g_alloc_count = 0;
+}
+
+cudaError_t dev_malloc(void **p, size_t bytes) {
+    if (fault_injected()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+cudaError_t dev_malloc_async(void **p, size_t bytes, cudaStream_t s) {
+    if (fault_injected()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMallocAsync(p, bytes, s);
 }
 
 void set_error(const char *fmt, ...) {
@@ -337,7 +370,7 @@ int64_t spmv_get_panel_limit(void) { return g_panel_limit.load(); }
 
 int spmv_create(spmv_handle *out, int64_t m, int64_t n, int64_t nnz, const int32_t *d_rows, const int32_t *d_cols,
                 const void *d_vals, int32_t value_type, const spmv_config *cfg, void *stream) {
-    g_err[0] = 0;
+    entry_reset();
     if (!out) {
         set_error("spmv_create: NULL output handle");
         return SPMV_ERR_INVALID;
@@ -378,7 +411,7 @@ int spmv_create(spmv_handle *out, int64_t m, int64_t n, int64_t nnz, const int32
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&h->d_status), sizeof(unsigned));
+    if (e == cudaSuccess) e = dev_malloc(reinterpret_cast<void **>(&h->d_status), sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) {
         int st = cuda_status(e, "device query");
@@ -400,7 +433,7 @@ int spmv_create(spmv_handle *out, int64_t m, int64_t n, int64_t nnz, const int32
 }
 
 int spmv_set_config(spmv_handle h, const spmv_config *cfg, void *stream) {
-    g_err[0] = 0;
+    entry_reset();
     if (!h) {
         set_error("spmv_set_config: NULL handle");
         return SPMV_ERR_INVALID;
@@ -623,7 +656,7 @@ int spmv_export(spmv_handle h, int32_t array_id, void *d_dst, int64_t bytes, voi
 }
 
 int spmv_check(spmv_handle h, void *stream) {
-    g_err[0] = 0;
+    entry_reset();
     if (!h) {
         set_error("spmv_check: NULL handle");
         return SPMV_ERR_INVALID;

@@ -183,7 +183,7 @@ int build(spmv_batch *b, cudaStream_t s) {
         int64_t items;
         if (M.mode == 0) {
             const int64_t nch = (h->nnz + C - 1) / C;
-            SPMV_CUDA_TRY(cudaMalloc((void **)&b->metas[i], sizeof(int32_t) * (nch + 1)));
+            SPMV_CUDA_TRY(dev_malloc((void **)&b->metas[i], sizeof(int32_t) * (nch + 1)));
             SPMV_TRY(build_split_meta(h->rowptr, h->m, h->nnz, C, b->metas[i], s));
             M.meta0 = b->metas[i];
             M.part_off = chunks_total;
@@ -196,8 +196,8 @@ int build(spmv_batch *b, cudaStream_t s) {
     }
     b->total_items = off[b->count];
     SPMV_TRY(alloc_partials(&b->part, chunks_total, 1, b->vt, s));
-    SPMV_CUDA_TRY(cudaMalloc(&b->d_mats, sizeof(BatchMat) * std::max(1, b->count)));
-    SPMV_CUDA_TRY(cudaMalloc((void **)&b->d_item_off, sizeof(int64_t) * (b->count + 1)));
+    SPMV_CUDA_TRY(dev_malloc(&b->d_mats, sizeof(BatchMat) * std::max(1, b->count)));
+    SPMV_CUDA_TRY(dev_malloc((void **)&b->d_item_off, sizeof(int64_t) * (b->count + 1)));
     SPMV_CUDA_TRY(cudaMemcpyAsync(b->d_mats, mats.data(), sizeof(BatchMat) * b->count, cudaMemcpyHostToDevice, s));
     SPMV_CUDA_TRY(cudaMemcpyAsync(b->d_item_off, off.data(), sizeof(int64_t) * (b->count + 1),
                                   cudaMemcpyHostToDevice, s));
@@ -250,6 +250,7 @@ extern "C" {
 
 int spmv_batch_create(spmv_batch_handle *out, const spmv_handle *hs, int32_t count, const double *alpha,
                       const void *const *d_x, const double *beta, void *const *d_y, void *stream) {
+    entry_reset();
     if (!out || count < 0 || (count > 0 && (!hs || !alpha || !d_x || !beta || !d_y))) {
         set_error("spmv_batch_create: bad arguments");
         return SPMV_ERR_INVALID;
@@ -293,7 +294,7 @@ int spmv_batch_create(spmv_batch_handle *out, const spmv_handle *hs, int32_t cou
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cs, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_counter, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = dev_malloc((void **)&b->d_counter, sizeof(unsigned long long));
     int st = e == cudaSuccess ? SPMV_OK : cuda_status(e, "spmv_batch_create");
     if (st == SPMV_OK) st = build(b, (cudaStream_t)stream);
     if (st != SPMV_OK) {
@@ -308,6 +309,7 @@ int spmv_batch_create(spmv_batch_handle *out, const spmv_handle *hs, int32_t cou
 }
 
 int spmv_batch_launch(spmv_batch_handle b, void *stream) {
+    entry_reset();
     if (!b) {
         set_error("spmv_batch_launch: NULL batch");
         return SPMV_ERR_INVALID;
@@ -317,6 +319,7 @@ int spmv_batch_launch(spmv_batch_handle b, void *stream) {
 }
 
 int spmv_batch_tune(spmv_batch_handle b, void *stream) {
+    entry_reset();
     if (!b) {
         set_error("spmv_batch_tune: NULL batch");
         return SPMV_ERR_INVALID;
@@ -356,13 +359,13 @@ int spmv_batch_tune(spmv_batch_handle b, void *stream) {
             int64_t *d_off = nullptr;
             int st = SPMV_OK;
             if (mode == 0) {
-                if (cudaMalloc((void **)&meta, sizeof(int32_t) * (off[1] + 1)) != cudaSuccess) st = SPMV_ERR_OOM;
+                if (dev_malloc((void **)&meta, sizeof(int32_t) * (off[1] + 1)) != cudaSuccess) st = SPMV_ERR_OOM;
                 if (st == SPMV_OK) st = build_split_meta(h->rowptr, h->m, h->nnz, C, meta, s);
                 M.meta0 = meta;
                 if (st == SPMV_OK) st = alloc_partials(&one.part, off[1], 1, one.vt, s);
             }
-            if (st == SPMV_OK && (cudaMalloc((void **)&d_m, sizeof(BatchMat)) != cudaSuccess ||
-                                  cudaMalloc((void **)&d_off, sizeof(off)) != cudaSuccess))
+            if (st == SPMV_OK && (dev_malloc((void **)&d_m, sizeof(BatchMat)) != cudaSuccess ||
+                                  dev_malloc((void **)&d_off, sizeof(off)) != cudaSuccess))
                 st = SPMV_ERR_OOM;
             if (st == SPMV_OK) {
                 cudaMemcpyAsync(d_m, &M, sizeof(M), cudaMemcpyHostToDevice, s);

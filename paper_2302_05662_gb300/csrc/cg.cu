@@ -321,20 +321,30 @@ int build_plan(spmv_matrix *h, const void *d_b, void *d_x, double tol, int32_t m
     c->maxit = maxit;
     c->nparts = 4 * (h->sm_count > 0 ? h->sm_count : 152);
     const size_t vb = vec_size(h->vt) * (size_t)h->m;
-    SPMV_CUDA_TRY(cudaMalloc(&c->r, vb));
-    SPMV_CUDA_TRY(cudaMalloc(&c->p, vb));
-    SPMV_CUDA_TRY(cudaMalloc(&c->q, vb));
-    SPMV_CUDA_TRY(cudaMalloc(&c->part, sizeof(double) * 3 * c->nparts));
-    SPMV_CUDA_TRY(cudaMalloc(&c->hist, sizeof(double) * ((size_t)maxit + 1)));
-    SPMV_CUDA_TRY(cudaMalloc(&c->st, sizeof(CgState)));
-    SPMV_CUDA_TRY(cudaStreamCreateWithFlags(&c->cs, cudaStreamNonBlocking));
+    // a plan that fails half-built is released, so a later call with the
+    // same arguments builds it again instead of reusing it
+    auto fail = [&](int st) {
+        free_cg(h);
+        return st;
+    };
+    cudaError_t e = dev_malloc(&c->r, vb);
+    if (e == cudaSuccess) e = dev_malloc(&c->p, vb);
+    if (e == cudaSuccess) e = dev_malloc(&c->q, vb);
+    if (e == cudaSuccess) e = dev_malloc(&c->part, sizeof(double) * 3 * c->nparts);
+    if (e == cudaSuccess) e = dev_malloc(&c->hist, sizeof(double) * ((size_t)maxit + 1));
+    if (e == cudaSuccess) e = dev_malloc(&c->st, sizeof(CgState));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return fail(cuda_status(e, "spmv_cg plan"));
     // one eager product before capture: occupancy and carveout settings of
     // the kernel are resolved outside the capture
-    SPMV_TRY(run_spmv(h, 1.0, d_b, 0.0, c->q, s));
-    SPMV_CUDA_TRY(cudaStreamSynchronize(s));
-    const int st = h->vt == SPMV_F64 ? capture_cg<double>(h, c) : capture_cg<float>(h, c);
-    if (st != SPMV_OK) free_cg(h);
-    return st;
+    int st = run_spmv(h, 1.0, d_b, 0.0, c->q, s);
+    if (st == SPMV_OK) {
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = cuda_status(e, "spmv_cg plan");
+    }
+    if (st == SPMV_OK) st = h->vt == SPMV_F64 ? capture_cg<double>(h, c) : capture_cg<float>(h, c);
+    if (st != SPMV_OK) return fail(st);
+    return SPMV_OK;
 }
 
 }  // namespace
@@ -344,6 +354,7 @@ using namespace spmv;
 
 extern "C" int spmv_cg(spmv_handle h, const void *d_b, void *d_x, double tol, int32_t maxit, double *d_rho,
                        spmv_cg_result *out, void *stream) {
+    entry_reset();
     if (!h || !out) {
         set_error("spmv_cg: NULL handle or result");
         return SPMV_ERR_INVALID;

@@ -29,21 +29,21 @@ struct Tmp {
     ~Tmp() { if (p) cudaFreeAsync(p, s); }
     int alloc(size_t count, cudaStream_t stream) {
         s = stream;
-        cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&p),
+        cudaError_t e = dev_malloc_async(reinterpret_cast<void **>(&p),
                                         std::max<size_t>(count, 1) * sizeof(T), stream);
-        if (e != cudaSuccess) { p = nullptr; return cuda_status(e, "cudaMallocAsync(temp)"); }
+        if (e != cudaSuccess) { p = nullptr; return cuda_status(e, "dev_malloc_async(temp)"); }
         return SPMV_OK;
     }
 };
 
 template <typename T>
 int dalloc(T **p, size_t count) {
-    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), std::max<size_t>(count, 1) * sizeof(T));
+    cudaError_t e = dev_malloc(reinterpret_cast<void **>(p), std::max<size_t>(count, 1) * sizeof(T));
     if (e != cudaSuccess) { *p = nullptr; return cuda_status(e, "cudaMalloc"); }
     return SPMV_OK;
 }
 int dalloc_bytes(void **p, size_t bytes) {
-    cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 1));
+    cudaError_t e = dev_malloc(p, std::max<size_t>(bytes, 1));
     if (e != cudaSuccess) { *p = nullptr; return cuda_status(e, "cudaMalloc"); }
     return SPMV_OK;
 }

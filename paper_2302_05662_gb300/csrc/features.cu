@@ -7,8 +7,9 @@
 // seconds per matrix); here three kernels read the CSR arrays once:
 //   k_feat_rows     row lengths: sum of squares, min, max, empty rows and a
 //                   histogram of lengths;
-//   k_feat_entries  per nonzero: |i - j| (max and sum), diagonal entries and
-//                   whether the entry opens a new 2x2 / 4x4 block;
+//   k_feat_entries  per nonzero, in equal chunks of nonzeros: |i - j| (max
+//                   and sum), diagonal entries and whether the entry opens a
+//                   new 2x2 / 4x4 block;
 //   k_feat_finish   one block: median, mode, Gini and the HYB width from the
 //                   histogram, then the 20 feature values.
 // Counts are exact 64-bit integers; ratios are formed once at the end.
@@ -94,19 +95,45 @@ __device__ __forceinline__ bool earlier_rows_hit(const int *rowptr, const int *c
     return false;
 }
 
-// One warp per row; lanes stride over the row's entries.  An entry opens a
-// new r x r block when no earlier entry of its block (earlier rows of the
-// block row, or the previous entry of its own row) lies in it.
+// largest r in [lo, hi] with rowptr[r] <= k (the row holding entry k)
+__device__ __forceinline__ int64_t row_in(const int *rowptr, int64_t lo, int64_t hi, int64_t k) {
+    while (lo < hi) {
+        const int64_t mid = lo + ((hi - lo + 1) >> 1);
+        if (rowptr[mid] <= k) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Nonzero chunks of FEAT_CHUNK entries, one warp each, so a power-law row
+// costs no more than the same number of entries in short rows: lane 0 finds
+// the rows of the chunk's first and last entries, every lane then finds the
+// row of each of its entries by a binary search between them.  Per entry:
+// |i - j|, the diagonal, and whether the entry opens a new r x r block (no
+// earlier entry of its block: neither the previous entry of its own row nor
+// an entry of an earlier row of the same block row).
 // row0: the global index of local row 0 (a multiple of 4 for row panels)
-__global__ void k_feat_entries(const int *rowptr, const int *colidx, int64_t m, int64_t row0, FeatAcc *acc) {
+constexpr int FEAT_CHUNK = 256;
+
+__global__ void k_feat_entries(const int *rowptr, const int *colidx, int64_t m, int64_t nnz, int64_t row0,
+                               FeatAcc *acc) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nchunks = (nnz + FEAT_CHUNK - 1) / FEAT_CHUNK;
     unsigned long long sd = 0, dg = 0, b4 = 0, b2 = 0;
     int md = 0;
-    for (int64_t i = warp; i < m; i += nwarps) {
-        const int b = rowptr[i], e = rowptr[i + 1];
-        for (int k = b + lane; k < e; k += 32) {
+    for (int64_t c = warp; c < nchunks; c += nwarps) {
+        const int64_t k0 = c * FEAT_CHUNK, k1 = k0 + FEAT_CHUNK < nnz ? k0 + FEAT_CHUNK : nnz;
+        int64_t r0 = 0, r1 = 0;
+        if (lane == 0) {
+            r0 = row_in(rowptr, 0, m - 1, k0);
+            r1 = row_in(rowptr, r0, m - 1, k1 - 1);
+        }
+        r0 = __shfl_sync(FULL, r0, 0);
+        r1 = __shfl_sync(FULL, r1, 0);
+        for (int64_t k = k0 + lane; k < k1; k += 32) {
+            const int64_t i = row_in(rowptr, r0, r1, k);
+            const int b = rowptr[i];
             const int j = colidx[k];
             const int64_t gi = row0 + i;
             const int64_t d = gi > j ? gi - j : j - gi;
@@ -244,7 +271,7 @@ int compute_features(const spmv_matrix *h, double *d_out, cudaStream_t s) {
     const int maxlen = (int)h->max_row;
     void *buf = nullptr;
     const size_t hist_bytes = sizeof(unsigned) * ((size_t)maxlen + 1);
-    SPMV_CUDA_TRY(cudaMallocAsync(&buf, hist_bytes + 256, s));
+    SPMV_CUDA_TRY(dev_malloc_async(&buf, hist_bytes + 256, s));
     unsigned *hist = static_cast<unsigned *>(buf);
     FeatAcc *acc = reinterpret_cast<FeatAcc *>(static_cast<char *>(buf) + (hist_bytes + 127) / 128 * 128);
     int st = SPMV_OK;
@@ -260,9 +287,10 @@ int compute_features(const spmv_matrix *h, double *d_out, cudaStream_t s) {
             if (mq == 0) continue;
             const int64_t blocks = (mq + 255) / 256;
             k_feat_rows<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(q->rowptr, mq, hist, acc);
-            const int64_t wblocks = (mq + 7) / 8;
-            k_feat_entries<<<(unsigned)(wblocks < 8192 ? wblocks : 8192), 256, 0, s>>>(q->rowptr, q->colidx, mq,
-                                                                                        row0, acc);
+            const int64_t wblocks = ((q->nnz + FEAT_CHUNK - 1) / FEAT_CHUNK + 7) / 8;
+            if (wblocks > 0)
+                k_feat_entries<<<(unsigned)(wblocks < 8192 ? wblocks : 8192), 256, 0, s>>>(q->rowptr, q->colidx, mq,
+                                                                                            q->nnz, row0, acc);
         }
         k_feat_finish<<<1, FIN_THREADS, 0, s>>>(hist, maxlen, m, h->n, h->nnz, acc, d_out);
         e = cudaGetLastError();

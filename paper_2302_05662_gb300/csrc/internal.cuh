@@ -20,6 +20,25 @@ namespace spmv {
 void set_error(const char *fmt, ...);
 int cuda_status(cudaError_t e, const char *what);
 
+// Every device allocation of the library goes through these two, so that
+// the host-side fault injector can fail one of them: with the environment
+// variable SPMV_FAULT_ALLOC=k, the k-th allocation of an entry-point call
+// returns cudaErrorMemoryAllocation without allocating (the call must then
+// return SPMV_ERR_OOM and release what it had allocated).  entry_reset(),
+// called first by every entry point that allocates, clears the thread's
+// error message and its allocation count.
+cudaError_t dev_malloc(void **p, size_t bytes);
+cudaError_t dev_malloc_async(void **p, size_t bytes, cudaStream_t s);
+template <typename T>
+inline cudaError_t dev_malloc(T **p, size_t bytes) {
+    return dev_malloc(reinterpret_cast<void **>(p), bytes);
+}
+template <typename T>
+inline cudaError_t dev_malloc_async(T **p, size_t bytes, cudaStream_t s) {
+    return dev_malloc_async(reinterpret_cast<void **>(p), bytes, s);
+}
+void entry_reset();
+
 #define SPMV_CUDA_TRY(expr)                                       \
     do {                                                          \
         cudaError_t _e = (expr);                                  \

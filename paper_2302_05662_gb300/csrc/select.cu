@@ -120,7 +120,7 @@ int run_selector(const spmv_matrix *h, const Selector *sel, cudaStream_t s, doub
     char *buf = nullptr;
     const size_t fb = sizeof(double) * SPMV_NUM_FEATURES;
     const size_t tb = th ? sizeof(float) * (sel->K + 1) : 0;
-    SPMV_CUDA_TRY(cudaMallocAsync((void **)&buf, fb + 16 + tb + 16, s));
+    SPMV_CUDA_TRY(dev_malloc_async((void **)&buf, fb + 16 + tb + 16, s));
     double *d_f = reinterpret_cast<double *>(buf);
     int *d_c = reinterpret_cast<int *>(buf + fb);
     float *d_t = reinterpret_cast<float *>(buf + fb + 16);
@@ -154,13 +154,14 @@ using namespace spmv;
 extern "C" {
 
 int spmv_features(spmv_handle h, double *h_out, void *stream) {
+    entry_reset();
     if (!h || !h_out) {
         set_error("spmv_features: NULL argument");
         return SPMV_ERR_INVALID;
     }
     cudaStream_t s = (cudaStream_t)stream;
     double *d = nullptr;
-    SPMV_CUDA_TRY(cudaMallocAsync((void **)&d, sizeof(double) * SPMV_NUM_FEATURES, s));
+    SPMV_CUDA_TRY(dev_malloc_async((void **)&d, sizeof(double) * SPMV_NUM_FEATURES, s));
     int st = compute_features(h, d, s);
     if (st == SPMV_OK) {
         cudaError_t e = cudaMemcpyAsync(h_out, d, sizeof(double) * SPMV_NUM_FEATURES, cudaMemcpyDeviceToHost, s);
@@ -172,6 +173,7 @@ int spmv_features(spmv_handle h, double *h_out, void *stream) {
 }
 
 int spmv_selector_load(const float *h_blob, int64_t count) {
+    entry_reset();
     if (!h_blob && count == 0) {  // unload: spmv_select falls back to default CSR
         Selector *sel = current_selector(nullptr);
         if (!sel) {
@@ -223,7 +225,7 @@ int spmv_selector_load(const float *h_blob, int64_t count) {
     std::vector<float> w(h_blob + 5, h_blob + 5 + nw1);
     const float *tail = h_blob + 5 + nw1 + (int64_t)K * NCFG;
     w.insert(w.end(), tail, tail + nw2);
-    SPMV_CUDA_TRY(cudaMalloc((void **)&sel->d_w, sizeof(float) * w.size()));
+    SPMV_CUDA_TRY(dev_malloc((void **)&sel->d_w, sizeof(float) * w.size()));
     SPMV_CUDA_TRY(cudaMemcpy(sel->d_w, w.data(), sizeof(float) * w.size(), cudaMemcpyHostToDevice));
     sel->labels.assign(K, spmv_config{});
     for (int k = 0; k < K; ++k) {
@@ -247,6 +249,7 @@ int spmv_selector_load(const float *h_blob, int64_t count) {
 }
 
 int spmv_selector_infer(const double *h_features, float *h_logits, int32_t *choice, void *stream) {
+    entry_reset();
     if (!h_features || !choice) {
         set_error("spmv_selector_infer: NULL argument");
         return SPMV_ERR_INVALID;
@@ -259,7 +262,7 @@ int spmv_selector_infer(const double *h_features, float *h_logits, int32_t *choi
     cudaStream_t s = (cudaStream_t)stream;
     char *buf = nullptr;
     const size_t fb = sizeof(double) * SPMV_NUM_FEATURES, lb = sizeof(float) * sel->K;
-    SPMV_CUDA_TRY(cudaMallocAsync((void **)&buf, fb + 16 + lb, s));
+    SPMV_CUDA_TRY(dev_malloc_async((void **)&buf, fb + 16 + lb, s));
     double *d_f = reinterpret_cast<double *>(buf);
     int *d_c = reinterpret_cast<int *>(buf + fb);
     float *d_l = reinterpret_cast<float *>(buf + fb + 16);
@@ -277,6 +280,7 @@ int spmv_selector_infer(const double *h_features, float *h_logits, int32_t *choi
 }
 
 int spmv_select(spmv_handle h, spmv_config *out_cfg, double *h_features, void *stream) {
+    entry_reset();
     if (!h || !out_cfg) {
         set_error("spmv_select: NULL argument");
         return SPMV_ERR_INVALID;
@@ -293,6 +297,7 @@ int spmv_select(spmv_handle h, spmv_config *out_cfg, double *h_features, void *s
 
 int spmv_select_runtime(spmv_handle h, int64_t expected_runs, spmv_config *out_cfg, spmv_runtime_decision *out,
                         void *stream) {
+    entry_reset();
     if (!h || !out_cfg || !out || expected_runs < 0) {
         set_error("spmv_select_runtime: bad argument");
         return SPMV_ERR_INVALID;
