@@ -30,7 +30,7 @@ bool fault_injected() {
 }  // namespace
 
 void entry_reset() {
-    entry_reset();
+    g_err[0] = 0;
     g_alloc_count = 0;
 }
 
