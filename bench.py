@@ -70,6 +70,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--only", default=None, help="comma-separated matrix names (profiling runs)")
     p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--mode", default="replicas", choices=["replicas", "shard"],
+                   help="N > 1: independent replicas of the step (weak scaling), or every product sharded "
+                        "by nnz-balanced row blocks with an all-gather of x (strong scaling)")
     p.add_argument("--fixed", default=None,
                    help="profiling runs: skip tuning and selection, run this kernel variant's default "
                         "configuration (csr, csr_split, ell, coo, hyb, bsr)")
@@ -858,6 +861,82 @@ def ours(args, world, rank, local):
         B.spmv_destroy(p["h"])
 
 
+def shard_bench(args, world, rank, local):
+    """Strong scaling of the step: every matrix is split into nnz-balanced
+    row blocks, one per rank (each rank's block a handle in the configuration
+    the selector picks for it); x lives in equal blocks and one all-gather
+    per product assembles it on every rank.  value = the step's flops over
+    the slowest rank's time."""
+    import torch
+    import torch.distributed as dist
+    from paper_2302_05662_gb300 import binding as B
+    from paper_2302_05662_gb300 import build as build_mod
+    from paper_2302_05662_gb300 import matgen, replicas, shard, sweep
+    from paper_2302_05662_gb300 import selector as S
+
+    torch.cuda.set_device(local)
+    if rank == 0 or world == 1:
+        build_mod.build()
+    if world > 1:
+        dist.barrier()
+    B.load_library()
+    if os.path.exists(S.DEFAULT_BLOB):
+        S.load_default_selector()
+    xdt = torch.float64 if args.dtype == "f64" else torch.float32
+    only = set(args.only.split(",")) if args.only else None
+    mats, flops = [], 0
+    for k, (mname, coo) in enumerate(matgen.workload_matrices(args.scale, only=only)):
+        rp = np.zeros(coo.m + 1, np.int64)
+        np.cumsum(np.bincount(coo.rows, minlength=coo.m), out=rp[1:])
+        bounds = shard.partition_rows(rp, world)
+        r0, r1 = int(bounds[rank]), int(bounds[rank + 1])
+        lr, lc, lv = shard.local_triplets(coo.rows, coo.cols, coo.vals, r0, r1)
+        sub = matgen.Coo(r1 - r0, coo.n, lr.astype(np.int32), lc, lv)
+        rows, cols, vals = sweep.device_matrix(sub, args.dtype)
+        sm = shard.ShardedMatrix(coo.m, coo.n, rows + r0, cols, vals, bounds, rank, world)
+        del rows, cols, vals
+        cfg, _ = B.spmv_select(sm.h)
+        B.spmv_set_config(sm.h, cfg)
+        x = matgen.dense_vector(coo.n, 100 + k)
+        xl = torch.zeros(sm.blk, dtype=xdt)
+        part = x[rank * sm.blk:(rank + 1) * sm.blk]
+        xl[:part.size] = torch.from_numpy(part)
+        mats.append((sm, xl.cuda(), torch.zeros(r1 - r0, dtype=xdt, device="cuda")))
+        flops += 2 * coo.nnz
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for sm, xl, y in mats:
+            sm.run(1.0, xl, 0.0, y, stream=stream.cuda_stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = replicas.max_over_ranks(e0.elapsed_time(e1), device="cuda")
+    value = flops * args.steps / (ms * 1e-3) / 1e9
+    if rank == 0:
+        cfgd = workload_config(args)
+        cfgd["parallelism"] = f"rowshard{world}"
+        print(json.dumps({"metric": "SpMV GFLOP/s (row-block sharded product, 5 format-sweep matrices)",
+                          "value": round(value, 2), "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+                          "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
+                          "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+                          "dtype": args.dtype, "data": "synthetic", "config": cfgd,
+                          "gpu_launches": None}), flush=True)
+    for sm, _, _ in mats:
+        sm.destroy()
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
@@ -869,7 +948,10 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
-    ours(args, world, rank, local)
+    if args.mode == "shard":
+        shard_bench(args, world, rank, local)
+    else:
+        ours(args, world, rank, local)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

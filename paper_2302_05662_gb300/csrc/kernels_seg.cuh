@@ -288,8 +288,13 @@ __device__ __forceinline__ void csr_split_chunk(int64_t c, int64_t nnz, int64_t 
 // the next multiple of 8 entries past nnz (their allocations are padded).
 // ---------------------------------------------------------------------------
 struct TileSmem {
-    int stage_bytes, cols_off, vals_off, rows_off, hdr_off, bar_off, list_off, red_off, total;
+    int stage_bytes, cols_off, vals_off, rows_off, hdr_off, bar_off, list_off, med_off, red_off, total;
 };
+
+// row segments per tile handed to whole warps (longer than a lane group
+// should sum alone, shorter than the block-wide threshold); a tile whose
+// medium segments overflow the list sends the rest to the block-wide pass
+constexpr int TILE_MED = 256;
 
 // Rows of a tile whose row pointers are staged with it: at most TILE_ROWS + 1
 // pointers (a tile with more rows, i.e. many empty rows, reads them from
@@ -309,7 +314,8 @@ __host__ __device__ inline TileSmem tile_smem_layout(int tile, int long_max) {
     L.stage_bytes = L.hdr_off + 128;
     L.bar_off = 2 * L.stage_bytes;                 // two stages, then 2 mbarriers
     L.list_off = L.bar_off + 16;                   // long segments: int4 (row, begin, end, -) + count
-    L.red_off = L.list_off + 16 * long_max + 16;   // block reduction scratch: 32 doubles
+    L.med_off = L.list_off + 16 * long_max + 16;   // medium segments: int4 x TILE_MED + count
+    L.red_off = L.med_off + 16 * TILE_MED + 16;    // block reduction scratch: 32 doubles
     L.total = L.red_off + 32 * 8;
     return L;
 }
@@ -325,6 +331,8 @@ k_csr_tiles(int64_t nnz, int64_t m, int64_t ntiles, int tile, int long_len, int 
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar_off);
     int4 *list = reinterpret_cast<int4 *>(smem + L.list_off);
     int *nlist = reinterpret_cast<int *>(smem + L.list_off + 16 * long_max);
+    int4 *med = reinterpret_cast<int4 *>(smem + L.med_off);
+    int *nmed = reinterpret_cast<int *>(smem + L.med_off + 16 * TILE_MED);
     T *red = reinterpret_cast<T *>(smem + L.red_off);
     const Epi<T> ep(alpha, beta);
     const int tid = threadIdx.x, lane = tid & 31;
@@ -360,6 +368,7 @@ k_csr_tiles(int64_t nnz, int64_t m, int64_t ntiles, int tile, int long_len, int 
         mbar_init(bar, 1);
         mbar_init(bar + 1, 1);
         *nlist = 0;
+        *nmed = 0;
         mbar_init_fence();
     }
     __syncthreads();
@@ -407,10 +416,11 @@ k_csr_tiles(int64_t nnz, int64_t m, int64_t ntiles, int tile, int long_len, int 
             }
             const int s = rs > E0 ? rs : (int)E0, e = rend < E1 ? rend : (int)E1;
             if (s >= e) continue;
-            if (e - s > long_len) {  // left to the whole block below
+            if (e - s > 2 * TPR * UNROLL && TPR < 32) {  // left to a whole warp, or the whole block
                 if (sub == 0) {
-                    const int i = atomicAdd(nlist, 1);
-                    if (i < long_max) list[i] = make_int4(r, s, e, 0);
+                    int i = e - s > long_len ? TILE_MED : atomicAdd(nmed, 1);
+                    if (i < TILE_MED) med[i] = make_int4(r, s, e, 0);
+                    else if ((i = atomicAdd(nlist, 1)) < long_max) list[i] = make_int4(r, s, e, 0);
                 }
                 continue;
             }
@@ -439,6 +449,37 @@ k_csr_tiles(int64_t nnz, int64_t m, int64_t ntiles, int tile, int long_len, int 
             }
         }
         __syncthreads();
+        // medium segments: one warp each, lanes striding, a shuffle sum
+        const int nm = *nmed < TILE_MED ? *nmed : TILE_MED;
+        for (int i = tid >> 5; i < nm; i += (int)(blockDim.x >> 5)) {
+            const int4 d = med[i];
+            T acc = T(0);
+            for (int q = d.y + lane; q < d.z; q += 32 * UNROLL) {
+                int c[UNROLL];
+                T v[UNROLL], xv[UNROLL];
+#pragma unroll
+                for (int u = 0; u < UNROLL; ++u) {
+                    const int qq = q + 32 * u;
+                    c[u] = qq < d.z ? sc[qq - E0] : -1;
+                    v[u] = qq < d.z ? (T)sv[qq - E0] : T(0);
+                }
+#pragma unroll
+                for (int u = 0; u < UNROLL; ++u) xv[u] = c[u] >= 0 ? ld_x(x, c[u]) : T(0);
+#pragma unroll
+                for (int u = 0; u < UNROLL; ++u)
+                    if (c[u] >= 0) acc = fma(v[u], xv[u], acc);
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+            if (lane == 0) {
+                const int rs = rp(d.x), rend = rp(d.x + 1);
+                T total = acc;
+                if (rs >= E0 && rend <= E1) ep.store(y, d.x, total);
+                else if (join_partial<T>(t, rs / tile, (rend - 1) / tile, 0, acc, P, &total))
+                    ep.store(y, d.x, total);
+            }
+        }
+        __syncthreads();  // every warp is done with the medium list before its reset and the stage refill
         const int nl = *nlist < long_max ? *nlist : long_max;
         for (int i = 0; i < nl; ++i) {  // long row segments: every thread strides, then a block sum
             const int4 d = list[i];
@@ -462,6 +503,7 @@ k_csr_tiles(int64_t nnz, int64_t m, int64_t ntiles, int tile, int long_len, int 
         // stage st is free: the block's tile after next goes into it
         if (tid == 0) {
             *nlist = 0;
+            *nmed = 0;
             if (tn < ntiles) {
                 fence_proxy_async_smem();
                 issue(tn, st, nrb, nre);
