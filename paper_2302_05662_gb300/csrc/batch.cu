@@ -51,40 +51,23 @@ struct BatchMat {
     int pad;
 };
 
-// Work items a warp takes per atomic grab: consecutive items mostly belong
-// to one matrix, so the grab's matrix lookup and descriptor load serve
-// several items, and the counter sees a quarter of the atomics.
-constexpr int BATCH_GRAB = 4;
-
 template <typename V, typename T, int ITEMS>
 __global__ void __launch_bounds__(512)
 k_batch(const BatchMat *__restrict__ mats, int count, const int64_t *__restrict__ item_off, int64_t total,
         unsigned long long *counter, const PartialsT<T> P) {
     const int lane = threadIdx.x & 31;
-    // the next grab is requested while the current one is processed
-    unsigned long long next = 0;
-    if (lane == 0) next = atomicAdd(counter, (unsigned long long)BATCH_GRAB);
-    int cur = -1;            // matrix of the previous item
-    int64_t cur_lo = 0, cur_hi = 0;
     for (;;) {
-        const unsigned long long grab = __shfl_sync(0xffffffffu, next, 0);
-        if (grab >= (unsigned long long)total) break;
-        if (lane == 0) next = atomicAdd(counter, (unsigned long long)BATCH_GRAB);
-        const unsigned long long gend =
-            grab + BATCH_GRAB < (unsigned long long)total ? grab + BATCH_GRAB : (unsigned long long)total;
-        for (unsigned long long item = grab; item < gend; ++item) {
-        if (cur < 0 || (int64_t)item < cur_lo || (int64_t)item >= cur_hi) {
-            int lo = 0, hi = count - 1;  // matrix owning the item
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if ((unsigned long long)__ldg(item_off + mid) <= item) lo = mid; else hi = mid - 1;
-            }
-            cur = lo;
-            cur_lo = __ldg(item_off + lo);
-            cur_hi = __ldg(item_off + lo + 1);
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(counter, 1ull);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= (unsigned long long)total) break;
+        int lo = 0, hi = count - 1;  // matrix owning the item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if ((unsigned long long)__ldg(item_off + mid) <= item) lo = mid; else hi = mid - 1;
         }
-        const BatchMat &M = mats[cur];
-        const int64_t local = (int64_t)item - cur_lo;
+        const BatchMat M = mats[lo];
+        const int64_t local = (int64_t)item - __ldg(item_off + lo);
         const Epi<T> ep((T)M.alpha, (T)M.beta);
         const V *vals = (const V *)M.vals;
         const T *x = (const T *)M.x;
@@ -107,7 +90,6 @@ k_batch(const BatchMat *__restrict__ mats, int count, const int64_t *__restrict_
             case 16: csr_vector_rows<V, T, 16, 2>(base, M.m, M.rowptr, M.colidx, vals, x, y, ep, big); break;
             default: csr_vector_rows<V, T, 32, 2>(base, M.m, M.rowptr, M.colidx, vals, x, y, ep, big); break;
             }
-        }
         }
     }
 }

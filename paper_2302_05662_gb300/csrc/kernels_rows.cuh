@@ -404,8 +404,13 @@ k_sell(int64_t m, int64_t nitems, const int *__restrict__ it_slice, const int *_
     for (int64_t j = 0; j * nwarps < nitems; ++j) {
         const int64_t it = j * nwarps + ((j & 1) ? nwarps - 1 - warp : warp);
         if (it >= nitems) continue;
-        // an item is three independent loads: slice, slot offset, columns
+        // an item is three independent loads: slice, slot offset, columns;
+        // the row this lane writes and the item's join range are requested
+        // with them, so their latency overlaps the item's loads
         const int sl = __ldg(it_slice + it), ib = __ldg(it_base + it), len = __ldg(it_len + it);
+        const int64_t c0 = __ldg(it_c0 + it), c1 = __ldg(it_c1 + it);
+        const int64_t p = (int64_t)sl * 32 + lane;
+        const int row = p < m ? __ldg(perm + p) : -1;
         const int64_t base = (int64_t)ib + lane;
         T acc = T(0);
         int k = 0;
@@ -427,10 +432,7 @@ k_sell(int64_t m, int64_t nitems, const int *__restrict__ it_slice, const int *_
             const int c = ld_s(col + base + 32LL * k);
             if (c >= 0) acc = fma(ld_val(val + base + 32LL * k), ld_x(x, c), acc);
         }
-        const int64_t p = (int64_t)sl * 32 + lane;
         if (p < m) {
-            const int row = __ldg(perm + p);
-            const int64_t c0 = __ldg(it_c0 + it), c1 = __ldg(it_c1 + it);
             T total = acc;
             if (c0 == c1 || join_partial<T>(it, c0, c1, lane, acc, P, &total)) ep.store(y, row, total);
         }

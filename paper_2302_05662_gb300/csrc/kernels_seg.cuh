@@ -416,7 +416,7 @@ k_csr_tiles(int64_t nnz, int64_t m, int64_t ntiles, int tile, int long_len, int 
             }
             const int s = rs > E0 ? rs : (int)E0, e = rend < E1 ? rend : (int)E1;
             if (s >= e) continue;
-            if (e - s > 2 * TPR * UNROLL && TPR < 32) {  // left to a whole warp, or the whole block
+            if (e - s > 8 * TPR * UNROLL && TPR < 32) {  // left to a whole warp, or the whole block
                 if (sub == 0) {
                     int i = e - s > long_len ? TILE_MED : atomicAdd(nmed, 1);
                     if (i < TILE_MED) med[i] = make_int4(r, s, e, 0);

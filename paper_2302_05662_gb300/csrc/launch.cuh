@@ -280,10 +280,10 @@ int launch_tiles(const spmv_matrix *h, T alpha, const T *x, T beta, T *y, cudaSt
     auto kern = k_csr_tiles<V, T, TPR, U>;
     const int tpb = h->cfg.threads_per_block < TPR ? TPR : h->cfg.threads_per_block;
     const int tile = 32 * h->seg.items;
-    // a row segment longer than 2 gathers per lane of its group goes to a
+    // a row segment longer than 8 gathers per lane of its group goes to a
     // whole warp, one longer than 8 gathers per lane of a warp to the block
     const int long_len = 8 * 32 * U;
-    const int long_max = tile / (2 * TPR * U + 1) + 2;  // room for every segment the groups pass on
+    const int long_max = tile / (8 * TPR * U + 1) + 2;  // room for every segment the groups pass on
     const TileSmem L = tile_smem_layout<V>(tile, long_max);
     SPMV_CUDA_TRY(cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total));
     SPMV_TRY(apply_carveout((const void *)kern, h->cfg.carveout));
