@@ -610,8 +610,20 @@ __global__ void k_sell_item_count(const int *sptr, int64_t nslices, int kmax, in
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t sl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; sl < nslices; sl += stride) {
         const int width = (sptr[sl + 1] - sptr[sl]) / 32;
-        cnt[sl] = width == 0 ? 1 : (width + kmax - 1) / kmax;
+        cnt[sl] = (width + kmax - 1) / kmax;  // zero-width slices (empty rows) get no item
     }
+}
+
+// first zero-width slice: the first s with ptr[s] == ptr[nslices] (rows are
+// sorted by descending length, so every later slice is empty too)
+__global__ void k_sell_first_empty(const int *sptr, int64_t nslices, int *out) {
+    const int total = sptr[nslices];
+    int64_t lo = 0, hi = nslices;
+    while (lo < hi) {
+        const int64_t mid = lo + ((hi - lo) >> 1);
+        if (sptr[mid] >= total) hi = mid; else lo = mid + 1;
+    }
+    *out = (int)lo;
 }
 
 // item j of a slice: its slice, the slot offset of its first column
@@ -621,7 +633,7 @@ __global__ void k_sell_item_fill(const int *sptr, int64_t nslices, int kmax, con
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t sl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; sl < nslices; sl += stride) {
         const int width = (sptr[sl + 1] - sptr[sl]) / 32;
-        const int n = width == 0 ? 1 : (width + kmax - 1) / kmax;
+        const int n = (width + kmax - 1) / kmax;
         const int o = off[sl];
         for (int j = 0; j < n; ++j) {
             it_slice[o + j] = (int)sl;
@@ -1268,7 +1280,15 @@ int pack_sell(spmv_matrix *h, int kmax, cudaStream_t s) {
                                                            L.seg_begin, L.seg_end, L.seg_c0, L.seg_c1);
     SPMV_CUDA_TRY(cudaGetLastError());
     SPMV_TRY(alloc_partials(&L.part, nitems, 32, h->vt, s));
+    // rows of the zero-width slices are written by a grid-stride pass
+    Tmp<int> sz;
+    SPMV_TRY(sz.alloc(1, s));
+    k_sell_first_empty<<<1, 1, 0, s>>>(h->sell_ptr, nslices, sz.p);
+    SPMV_CUDA_TRY(cudaGetLastError());
+    int hz = 0;
+    SPMV_CUDA_TRY(cudaMemcpyAsync(&hz, sz.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     SPMV_CUDA_TRY(cudaStreamSynchronize(s));
+    L.nrows = hz;
     return SPMV_OK;
 }
 }  // namespace

@@ -386,18 +386,23 @@ k_bsr_long(int64_t nseg, const int *__restrict__ seg_row, const int *__restrict_
 // and little padding.  A work item covers at most the item width (128
 // columns by default) of one slice: a wider slice becomes several items whose
 // per-row partials are joined in item order, so a slice of power-law rows is
-// not left to one warp.
+// not left to one warp.  Slices of empty rows get no work item.
 // ---------------------------------------------------------------------------
 template <typename V, typename T, int UNROLL, int REGCAP>
 __global__ void __launch_bounds__(1024) __maxnreg__(REGCAP)
-k_sell(int64_t m, int64_t nitems, const int *__restrict__ it_slice, const int *__restrict__ it_base,
+k_sell(int64_t m, int64_t nitems, int64_t s_zero, const int *__restrict__ it_slice, const int *__restrict__ it_base,
        const int *__restrict__ it_len, const int *__restrict__ it_c0, const int *__restrict__ it_c1,
        const int *__restrict__ col, const V *__restrict__ val, const int *__restrict__ perm,
        const T *__restrict__ x, T *__restrict__ y, T alpha, T beta, const PartialsT<T> P) {
     const Epi<T> ep(alpha, beta);
     const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t warp = gtid >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    // empty rows (sorted last, in slices s_zero and after): no item, one
+    // grid-stride pass; the stable sort keeps their order, so the writes
+    // of consecutive threads go to increasing rows
+    for (int64_t p = s_zero * 32 + gtid; p < m; p += nwarps * 32) ep.store(y, __ldg(perm + p), T(0));
     // items come widest slice first; passes over the warps alternate
     // direction (warp w takes item w of pass 0, item 2N-1-w of pass 1, ...),
     // so the warps that drew the widest items draw the narrowest next

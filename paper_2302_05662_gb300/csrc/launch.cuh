@@ -188,10 +188,12 @@ int launch_sell_rc(const spmv_matrix *h, T alpha, const T *x, T beta, T *y, cuda
     auto kern = k_sell<V, T, U, RC>;
     const int tpb = h->cfg.threads_per_block;
     SPMV_TRY(apply_carveout((const void *)kern, h->cfg.carveout));
-    const LongRows &L = h->lng;
+    const LongRows &L = h->lng;  // items; nrows = first slice of empty rows
     const int64_t wpb = tpb / 32;
-    const int grid = wave_grid((const void *)kern, tpb, (L.nseg + wpb - 1) / wpb, h->sm_count);
-    kern<<<grid, tpb, 0, s>>>(h->m, L.nseg, L.seg_row, L.seg_begin, L.seg_end, L.seg_c0, L.seg_c1, h->sell_col,
+    const int64_t empty_rows = h->m - 32 * L.nrows > 0 ? h->m - 32 * L.nrows : 0;
+    const int64_t need = std::max((L.nseg + wpb - 1) / wpb, (empty_rows + tpb - 1) / tpb);
+    const int grid = wave_grid((const void *)kern, tpb, need, h->sm_count);
+    kern<<<grid, tpb, 0, s>>>(h->m, L.nseg, L.nrows, L.seg_row, L.seg_begin, L.seg_end, L.seg_c0, L.seg_c1, h->sell_col,
                               (const V *)h->sell_val, h->sell_perm, x, y, alpha, beta, PartialsT<T>::of(L.part));
     SPMV_LAUNCH_CHECK();
     return SPMV_OK;
