@@ -205,6 +205,57 @@ def calibrate_pack(indices, out_path, reps: int = 3):
                 B.spmv_destroy(h)
 
 
+def best_label(records_by_matrix: dict, idx: int):
+    """The fastest label configuration of matrix idx over its sweep records
+    (the main sweep and any supplementary format sweep), as a config dict."""
+    best = None
+    for rec in records_by_matrix.get(idx, []):
+        for key, us in rec["times"]:
+            if us is not None and (best is None or us < best[1]):
+                best = (key, us)
+    if best is None:
+        return None
+    return {kv.split("=")[0]: int(kv.split("=")[1]) for kv in best[0].split(",")}
+
+
+def refine_sweep(args, timer):
+    """Register cap x unroll x carveout (refine_space) around each matrix's
+    best label configuration from earlier sweep records, timed in one
+    session together with that configuration at the library defaults.
+    Appends {matrix, family, best, best_us, refine: [[key, us], ...]}."""
+    import gzip
+    import ast
+    by = {}
+    for path in args.refine_from:
+        with (gzip.open(path, "rt") if path.endswith(".gz") else open(path)) as fh:
+            for line in fh:
+                r = json.loads(line)
+                t = r["times"]
+                r["times"] = ast.literal_eval(t) if isinstance(t, str) else t
+                by.setdefault(r["matrix"], []).append(r)
+    done = set()
+    if os.path.exists(args.out):
+        with open(args.out) as fh:
+            done = {json.loads(l)["matrix"] for l in fh if l.strip()}
+    t0 = time.time()
+    with open(args.out, "a") as fh:
+        for idx in range(args.start, args.start + args.count):
+            if idx in done or idx not in by:
+                continue
+            if time.time() - t0 > args.time_budget:
+                break
+            best = best_label(by, idx)
+            if best is None:
+                continue
+            fam, coo = generate_dataset_matrix(idx, n_hi=args.n_hi)
+            space = [dict(best)] + refine_space(best)
+            res = sweep_matrix(coo, space, timer, reps=args.reps, value_dtype=args.dtype, seed=idx)
+            fh.write(json.dumps({"matrix": idx, "family": fam, "dtype": args.dtype, "best": config_key(best),
+                                 "best_us": res[0][1],
+                                 "refine": [[config_key(c), t] for c, t in res[1:]]}) + "\n")
+            fh.flush()
+
+
 def main():
     ap = argparse.ArgumentParser(description="exhaustive format/launch sweep")
     ap.add_argument("--start", type=int, default=0)
@@ -220,10 +271,16 @@ def main():
     ap.add_argument("--formats", default=None,
                     help="comma list (csr,ell,coo,hyb,bsr,sell): a supplementary sweep of these formats' "
                          "label points only, merged into earlier records by the selector trainer")
+    ap.add_argument("--refine-from", nargs="*", default=None,
+                    help="sweep records: time the register cap x unroll x carveout space around each "
+                         "matrix's best label configuration instead")
     args = ap.parse_args()
     from . import build
     build.build()
     B.load_library()
+    if args.refine_from:
+        refine_sweep(args, Timer())
+        return
     if args.calibrate_pack:
         calibrate_pack(range(args.start, args.start + args.count), args.out)
         return
