@@ -19,7 +19,8 @@
  *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
  *     stream.  All device work is ordered on that stream.  Calls that must
  *     learn a size on the host (create, set_config, features, select)
- *     synchronise that stream once; spmv_run never synchronises.
+ *     synchronise that stream once; spmv_run never synchronises (except in
+ *     the checked mode below).
  *   - Every function returns an spmv_status (0 = success).  On failure
  *     spmv_last_error() returns a message for the calling thread.  No C++
  *     exception or process exit crosses this boundary.
@@ -28,6 +29,12 @@
  *     accumulate in float.  Indices are int32 (m, n < 2^31, nnz < 2^31).
  *   - A handle is not thread-safe; runs on one handle must be ordered on
  *     one stream (they share the handle's reduction scratch).
+ *   - Checked products (a debug mode): with the environment variable
+ *     SPMV_CHECKED=1, spmv_run first verifies every stored index of the
+ *     active format against the matrix bounds (one extra pass and a
+ *     synchronisation of `stream`); a bad index sets the handle's status
+ *     word and spmv_run returns SPMV_ERR_BOUNDS without launching the
+ *     product.  Unset (the default), spmv_run does no such pass.
  *   - Fault injection (for testing callers' error paths): with the
  *     environment variable SPMV_FAULT_ALLOC=k (k >= 1), the k-th device
  *     allocation made inside each call fails as if the device were out of
@@ -203,7 +210,8 @@ SPMV_API int spmv_get_info(spmv_handle h, spmv_info *out);
  * One or two kernel launches on `stream` per row panel (one panel unless
  * the matrix has more triplets than the panel limit); never synchronises.
  * Errors: SPMV_ERR_INVALID for a NULL handle or a NULL vector with a
- * nonzero size; SPMV_ERR_CUDA if a launch fails.
+ * nonzero size; SPMV_ERR_CUDA if a launch fails; SPMV_ERR_BOUNDS in the
+ * checked mode (SPMV_CHECKED=1) when a stored index is out of bounds.
  */
 SPMV_API int spmv_run(spmv_handle h, double alpha, const void *d_x, double beta,
              void *d_y, void *stream);

@@ -554,6 +554,11 @@ int spmv_run(spmv_handle h, double alpha, const void *d_x, double beta, void *d_
         return SPMV_ERR_INVALID;
     }
     if (h->m == 0) return SPMV_OK;
+    if (checked_mode()) {  // debug mode: verify the stored indices first (checked.cu)
+        const int parts = h->npanels > 0 ? h->npanels : 1;
+        for (int p = 0; p < parts; ++p)
+            SPMV_TRY(check_indices(h->npanels > 0 ? h->panels[p] : h, (cudaStream_t)stream));
+    }
     return run_product(h, alpha, d_x, beta, d_y, (cudaStream_t)stream);
 }
 

@@ -348,6 +348,11 @@ int gather_panel(const int32_t *d_rows, const int32_t *d_cols, const void *d_val
                  int64_t r0, int64_t r1, int32_t **orow, int32_t **ocol, void **oval, int64_t *count,
                  cudaStream_t s);
 
+// checked products (checked.cu): SPMV_CHECKED=1 in the environment, and
+// the verification of the active format's indices before a product
+bool checked_mode();
+int check_indices(const spmv_matrix *h, cudaStream_t s);
+
 // y = alpha A x + beta y in the handle's current format (api.cu)
 int run_product(const spmv_matrix *h, double alpha, const void *x, double beta, void *y, cudaStream_t s);
 // release the conjugate-gradient plan (cg.cu); packs it captured go stale on re-pack

@@ -286,6 +286,101 @@ def evaluate(choice, T, D):
             "geomean_best_vs_default_csr": float(np.exp(np.mean(np.log(D / best))))}
 
 
+KNOBS = ("regcap", "unroll", "carveout")
+DEFAULT_KNOBS = (0, 0, -1)   # the library defaults (resolved per format and value type)
+
+
+def _parse_key(key: str) -> dict:
+    return {kv.split("=")[0]: int(kv.split("=")[1]) for kv in key.split(",")}
+
+
+def _class_key(d: dict) -> str:
+    from . import sweep
+    return sweep.config_key({k: v for k, v in d.items() if k not in KNOBS})
+
+
+def load_refine(paths) -> dict:
+    """Refine records by matrix: {matrix: (base class key, {knobs: us})},
+    knobs = (regcap, unroll, carveout), DEFAULT_KNOBS for the base point."""
+    import gzip
+    out = {}
+    for p in paths:
+        with (gzip.open(p, "rt") if p.endswith(".gz") else open(p)) as fh:
+            for line in fh:
+                if not line.strip():
+                    continue
+                r = json.loads(line)
+                t = {DEFAULT_KNOBS: r["best_us"]}
+                for key, us in r["refine"]:
+                    d = _parse_key(key)
+                    t[tuple(d[k] for k in KNOBS)] = us
+                out[r["matrix"]] = (_class_key(_parse_key(r["best"])), t)
+    return out
+
+
+def knob_table(refine: dict, train_ids) -> dict:
+    """The paper's compile-time knobs (Section 4 items 1-3: register cap,
+    memory configuration; plus unroll) chosen per label class from the
+    training matrices whose best class it is: the knob setting with the
+    smallest geometric-mean time relative to each matrix's refined best.
+    The library defaults are a candidate, so a class keeps them unless a
+    setting beats them on its matrices."""
+    by_class = {}
+    for mid in train_ids:
+        if mid not in refine:
+            continue
+        base, t = refine[mid]
+        ok = {k: v for k, v in t.items() if v is not None}
+        if not ok:
+            continue
+        best = min(ok.values())
+        by_class.setdefault(base, []).append({k: v / best for k, v in ok.items()})
+    table = {}
+    for base, mats in by_class.items():
+        cands = set().union(*[set(m) for m in mats])
+        score = {}
+        for c in cands:
+            rs = [m.get(c) for m in mats]
+            if any(r is None for r in rs):
+                continue
+            score[c] = float(np.exp(np.mean(np.log(rs))))
+        if score:
+            table[base] = min(score, key=score.get)
+    return table
+
+
+def evaluate_refined(choice_keys, ids, refine: dict, T, labels_keys, table: dict):
+    """Slowdown against the refined exhaustive best (the best label point
+    with its knobs refined) of the selector's choice, with and without the
+    knob table, on matrices that have refine records.  Times come from the
+    refine session; a choice other than the refined class is rescaled from
+    the main sweep by the ratio of the two sessions' times of that class."""
+    slow_k, slow_0 = [], []
+    kidx = {k: j for j, k in enumerate(labels_keys)}
+    for i, mid in enumerate(ids):
+        if mid not in refine:
+            continue
+        base, t = refine[mid]
+        ok = {k: v for k, v in t.items() if v is not None}
+        if not ok or base not in kidx or not np.isfinite(T[i, kidx[base]]):
+            continue
+        best = min(ok.values())
+        ck = choice_keys[i]
+        if ck == base:
+            t0 = ok.get(DEFAULT_KNOBS)
+            tk = ok.get(table.get(ck, DEFAULT_KNOBS), t0)
+        else:
+            scale = ok[DEFAULT_KNOBS] / T[i, kidx[base]]
+            t0 = tk = T[i, kidx[ck]] * scale
+        slow_0.append(t0 / best)
+        slow_k.append(tk / best)
+    def summ(v):
+        v = np.array(v)
+        return {"n": int(v.size), "within_10pct": float(np.mean(v <= 1.10)),
+                "geomean_slowdown": float(np.exp(np.mean(np.log(v)))), "median_slowdown": float(np.median(v))}
+    return {"with_knob_table": summ(slow_k), "class_only": summ(slow_0)}
+
+
 def main():
     """Train on the sweep records (matrices 0-1799), evaluate on 1800-1999,
     write the blob and a JSON report.  With --calib (conversion-time
@@ -302,6 +397,8 @@ def main():
     ap.add_argument("--holdout-start", type=int, default=1800)
     ap.add_argument("--from-blob", default=None, help="reuse this blob's classifier, fit only the heads")
     ap.add_argument("--calib", nargs="*", default=None, help="conversion-time records (JSON lines)")
+    ap.add_argument("--refine", nargs="*", default=None,
+                    help="refine records (sweep --refine-from): per-class register cap, unroll and carveout")
     args = ap.parse_args()
     recs = load_records(args.data)
     labels = sweep.label_space(include_sell=has_sell(recs))
@@ -378,6 +475,17 @@ def main():
                 agree[str(runs)] = hits / tot if tot else None
             report["gate_agreement_heldout"] = agree
         report["pack_model_us"] = {str(f): [float(v) for v in pack[f]] for f in range(NFMT)}
+    if args.refine:
+        refine = load_refine(args.refine)
+        table = knob_table(refine, ids[train_m])
+        labels = [dict(c, **dict(zip(KNOBS, table[keys[j]]))) if keys[j] in table else c
+                  for j, c in enumerate(labels)]
+        report["knob_table"] = {k: dict(zip(KNOBS, v)) for k, v in sorted(table.items())}
+        for name, msk in (("train", train_m), ("heldout", test_m)):
+            logits = np.where(np.isfinite(T[msk]), predict(w, X[msk]), -np.inf)
+            choice = np.argmax(logits, axis=1)
+            report[name + "_vs_refined_best"] = evaluate_refined([keys[c] for c in choice], ids[msk], refine,
+                                                                 T[msk], keys, table)
     blob = make_blob(w["mu"], w["sigma"], w["W1"], w["b1"], w["W2"], w["b2"], labels, W3, b3, pack)
     blob.tofile(args.out)
     txt = json.dumps(report, indent=1)

@@ -185,3 +185,52 @@ def test_status_word_stays_clear_on_valid_products(name):
         B.spmv_check(h)       # raises on a recorded timeout or bounds error
     finally:
         B.spmv_destroy(h)
+
+
+CHECK_CASES = [("rmat", lambda: matgen.rmat(12, 16, np.random.default_rng(21))),
+               ("banded", lambda: matgen.banded(6000, 32, np.random.default_rng(22)))]
+
+
+@pytest.mark.parametrize("vt", [B.SPMV_F64, B.SPMV_BF16])
+@pytest.mark.parametrize("case", [c[0] for c in CHECK_CASES])
+@pytest.mark.parametrize("name", [f[0] for f in FORMATS])
+def test_checked_products_equal_unchecked(name, case, vt):
+    """SPMV_CHECKED=1: the index pass finds nothing on valid matrices (status
+    word clear) and the product is bit-identical to the unchecked one
+    (bf16 on the banded matrix exercises ELL's 16-bit column offsets)."""
+    import torch
+    from gpu_util import run
+    coo = dict(CHECK_CASES)[case]()
+    try:
+        h = create(coo, vt, B.make_config(**dict(FORMATS)[name]))
+    except B.SpmvError as e:
+        assert e.status == -4          # a padded format over its storage limit
+        return
+    try:
+        x = matgen.dense_vector(coo.n, 12)
+        plain = run(h, vt, x, m=coo.m)
+        checked = _with_checked(lambda: run(h, vt, x, m=coo.m))
+        assert np.array_equal(plain, checked)
+        B.spmv_check(h)
+    finally:
+        B.spmv_destroy(h)
+
+
+def _with_checked(fn):
+    os.environ["SPMV_CHECKED"] = "1"
+    try:
+        return fn()
+    finally:
+        del os.environ["SPMV_CHECKED"]
+
+
+def test_parity_suite_passes_in_checked_mode():
+    """The whole parity module again, every product preceded by the index
+    pass (valid inputs only): every case must still match the oracle."""
+    import subprocess
+    import sys
+    here = os.path.dirname(os.path.abspath(__file__))
+    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(here, "test_gpu_parity.py"), "-q", "-x",
+                        "-m", "gpu", "-p", "no:cacheprovider"],
+                       env=dict(os.environ, SPMV_CHECKED="1"), capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-2000:]

@@ -134,3 +134,38 @@ def test_supplementary_records_merge_on_the_base_scale(tmp_path):
     assert tm["format=5,threads_per_block=64"] is None
     assert tm["format=0,threads_per_block=32,threads_per_row=1"] == 50.0
     assert S.has_sell(recs) and not S.has_sell(S.load_records([str(p1)]))
+
+
+def _refine(base, times):
+    """A refine record: base class key, {(regcap, unroll, carveout): us}."""
+    return (base, dict(times))
+
+
+def test_knob_table_picks_the_best_shared_setting():
+    A = "format=2,threads_per_block=32"
+    refine = {
+        0: _refine(A, {S.DEFAULT_KNOBS: 10.0, (32, 4, 0): 8.0, (64, 2, -1): 9.0}),
+        1: _refine(A, {S.DEFAULT_KNOBS: 20.0, (32, 4, 0): 17.0, (64, 2, -1): 15.0}),
+        2: _refine("format=1,threads_per_block=64", {S.DEFAULT_KNOBS: 5.0, (32, 1, 100): 6.0}),
+        3: _refine(A, {S.DEFAULT_KNOBS: 1.0, (32, 4, 0): 0.1}),            # held out: ignored
+    }
+    table = S.knob_table(refine, train_ids=[0, 1, 2])
+    # (32,4,0): geomean(8/8, 17/15) = 1.0646; (64,2,-1): geomean(9/8, 15/15) = 1.0607
+    assert table[A] == (64, 2, -1)
+    assert table["format=1,threads_per_block=64"] == S.DEFAULT_KNOBS   # defaults win there
+
+
+def test_evaluate_refined_uses_the_refine_session():
+    A, Bk = "format=2,threads_per_block=32", "format=5,threads_per_block=32"
+    keys = [A, Bk]
+    refine = {7: _refine(A, {S.DEFAULT_KNOBS: 10.0, (32, 4, 0): 8.0}),
+              8: _refine(A, {S.DEFAULT_KNOBS: 10.0, (32, 4, 0): 8.0})}
+    T = np.array([[20.0, 30.0], [20.0, 30.0]])     # main sweep: another session, 2x slower
+    table = {A: (32, 4, 0)}
+    r = S.evaluate_refined([A, Bk], np.array([7, 8]), refine, T, keys, table)
+    # matrix 7 chose its refined class: 8/8 with the table, 10/8 without;
+    # matrix 8 chose B: 30 * (10/20) = 15, against the refined best 8
+    assert r["with_knob_table"]["n"] == 2
+    assert np.isclose(r["with_knob_table"]["geomean_slowdown"], np.sqrt(1.0 * 15 / 8))
+    assert np.isclose(r["class_only"]["geomean_slowdown"], np.sqrt(10 / 8 * 15 / 8))
+    assert r["with_knob_table"]["within_10pct"] == 0.5
