@@ -366,15 +366,23 @@ def tune_matrix(B, sweep, h, coo, x, y, timer, reps):
     return best_cfg, best_t, per_fmt
 
 
-def batched_section(B, matgen, torch, count=512, seed=7, steps=20):
+def batched_section(B, matgen, torch, count=512, seed=7, steps=20, select=True):
     """512 uneven fp32 matrices: one graph-captured persistent launch (after
-    the autotuner) against one spmv_run per matrix."""
+    the autotuner) against one spmv_run per matrix.  With `select`, every
+    handle first takes the format the selector picks for it (the batch runs
+    ELL and SELL matrices in their format, the others from CSR)."""
     hs, xs, ys, nnz, nbytes = [], [], [], 0, 0
+    fmts = {}
     for i, coo in matgen.batched_workload(count, seed):
         r = torch.from_numpy(coo.rows).cuda()
         c = torch.from_numpy(coo.cols).cuda()
         v = torch.from_numpy(coo.vals).cuda().float()
         hs.append(B.spmv_create(coo.m, coo.n, r, c, v))
+        if select:
+            cfg, _ = B.spmv_select(hs[-1])
+            B.spmv_set_config(hs[-1], cfg)
+        f = FMT_KEYS[B.spmv_get_config(hs[-1]).format]
+        fmts[f] = fmts.get(f, 0) + 1
         xs.append(torch.from_numpy(matgen.dense_vector(coo.n, 9000 + i)).float().cuda())
         ys.append(torch.zeros(coo.m, dtype=torch.float32, device="cuda"))
         nnz += coo.nnz
@@ -431,9 +439,11 @@ def batched_section(B, matgen, torch, count=512, seed=7, steps=20):
             "speedup": round(t_sep / t_graph, 3),
             "separate_launches_graph_ms": round(t_sep_graph, 4),
             "speedup_vs_graph_of_launches": round(t_sep_graph / t_graph, 3),
+            "formats_selected": fmts,
             "plan": {"items": items, "threads_per_block": tpb,
-                     "split_matrices": int((modes == 0).sum()),
-                     "vector_matrices": int((modes != 0).sum())}}
+                     "ell_matrices": int((modes == -1).sum()), "sell_matrices": int((modes == -5).sum()),
+                     "csr_split_matrices": int((modes == 0).sum()),
+                     "csr_vector_matrices": int((modes > 0).sum())}}
 
 
 def cg_section(B, matgen, torch, S, have_v2, tol=1e-8, maxit=5000):

@@ -366,24 +366,29 @@ SPMV_API int spmv_select(spmv_handle h, spmv_config *out_cfg, double *h_features
  * Batched SpMV (a batch of independent products y_i <- alpha_i A_i x_i +
  * beta_i y_i in one persistent launch).  The paper runs one kernel per
  * matrix; a batch of hundreds of uneven matrices would then pay one launch
- * each.  A batch plan holds, for every matrix, a mode -- nonzero chunks of
- * 32*items entries per warp (split) or 32-row groups with 1..32 lanes per
- * row (vector) -- and a list of warp work items over all matrices that a
- * grid of resident thread blocks consumes through one atomic counter.  The
- * counter reset and the kernel are captured in a CUDA graph.
+ * each.  A batch plan holds, for every matrix, a mode and a list of warp
+ * work items over all matrices that a grid of resident thread blocks
+ * consumes through one atomic counter.  A matrix whose handle holds ELL or
+ * SELL runs in that format (ELL: 32 rows per item, a row per lane; SELL:
+ * the handle's work items; mode -1 and -5); any other handle runs from its
+ * CSR arrays as nonzero chunks of 32*items entries per warp (split, mode 0)
+ * or 32-row groups with 1..32 lanes per row (vector, mode = lanes per row).
+ * The counter reset and the kernel are captured in a CUDA graph.
  *
  * spmv_batch_create: hs[i] (all of one value type), alpha[i], beta[i] (host
  * arrays) and device vectors d_x[i] (n_i entries), d_y[i] (m_i entries), i <
- * count.  The plan reads the handles' CSR arrays: the handles and vectors
- * must outlive the plan and keep their addresses.  Default modes come from
+ * count.  The plan reads the handles' arrays (and a SELL handle's join
+ * scratch): the handles and vectors must outlive the plan, keep their
+ * addresses and formats, and not run other products while the plan does.  Default modes come from
  * row-length statistics.  Synchronises `stream`.
- * spmv_batch_tune: autotuner -- times every mode per matrix on one-matrix
- * launches, then the chunk size (items 4/8/16) and block size
+ * spmv_batch_tune: autotuner -- times every CSR mode per CSR matrix on
+ * one-matrix launches, then the chunk size (items 4/8/16) and block size
  * (128/256/512) on the whole batch, keeps the fastest and re-captures the
  * graph.  Overwrites y.  Synchronises `stream`.
  * spmv_batch_launch: replays the graph on `stream` (no synchronisation).
- * spmv_batch_get_plan: copies the per-matrix modes (0 = split, else lanes
- * per row; h_modes may be NULL), the items and the block size.
+ * spmv_batch_get_plan: copies the per-matrix modes (0 = split, lanes per
+ * row for vector CSR, -1 ELL, -5 SELL; h_modes may be NULL), the items and
+ * the block size.
  * spmv_batch_run: create + launch + destroy in one call (synchronises).
  * Errors: SPMV_ERR_INVALID (NULL arrays or handles, mixed value types),
  * SPMV_ERR_UNSUPPORTED (a handle held in row panels), SPMV_ERR_OOM,

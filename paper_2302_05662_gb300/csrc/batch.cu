@@ -1,8 +1,11 @@
 // Batched SpMV: hundreds of uneven matrices in one persistent launch.
 //
-// Each matrix contributes work items for one warp each: chunks of 32*ITEMS
-// nonzeros (split mode, for power-law or very short rows) or groups of 32
-// rows with a per-matrix number of lanes per row (vector mode).  A grid of
+// Each matrix contributes work items for one warp each, in the format its
+// handle holds: ELL (groups of 32 rows, a row per lane), SELL (the handle's
+// work items, plus groups of 32 of its empty rows), or otherwise CSR --
+// chunks of 32*ITEMS nonzeros (split mode, for power-law or very short rows)
+// or groups of 32 rows with a per-matrix number of lanes per row (vector
+// mode).  A grid of
 // resident thread blocks pulls items from one atomic counter, so small and
 // large matrices share the GPU without a launch per matrix.  The counter
 // reset and the kernel are captured once in a CUDA graph and replayed.  An
@@ -47,9 +50,61 @@ struct BatchMat {
     int64_t m, nnz;
     int64_t part_off;  // first chunk of this matrix in the batch partials
     const int *meta0;  // split: row of each chunk's first entry
-    int mode;          // 0 split, else lanes per row
-    int pad;
+    int mode;          // CSR: 0 split, else lanes per row
+    int fmt;           // the handle's format: SPMV_FMT_ELL, SPMV_FMT_SELL, or CSR (any other)
+    // ELL: column-major arrays, int32 columns or 16-bit offsets
+    const int *ell_col;
+    const int16_t *ell_d16;
+    const void *ell_val;
+    int64_t ell_width, ell_pitch;
+    // SELL: the handle's work items, arrays and partials; rows from slice
+    // s_zero on are empty
+    const int *it_slice, *it_base, *it_len, *it_c0, *it_c1;
+    const int *sell_col, *sell_perm;
+    const void *sell_val;
+    int64_t nitems, s_zero;
+    void *p_head, *p_tail;
+    unsigned *p_count;
+    unsigned long long *p_xslot;
 };
+
+// work items of one matrix: CSR split chunks or 32-row groups, ELL 32-row
+// groups, SELL items plus 32-row groups of its empty rows
+int64_t batch_items(const BatchMat &M, int C) {
+    if (M.fmt == SPMV_FMT_ELL) return (M.m + 31) / 32;
+    if (M.fmt == SPMV_FMT_SELL) return M.nitems + (std::max<int64_t>(0, M.m - 32 * M.s_zero) + 31) / 32;
+    return M.mode == 0 ? (M.nnz + C - 1) / C : (M.m + 31) / 32;
+}
+
+// the handle's active format as the batch runs it (ELL, SELL, else CSR modes)
+void describe_format(const spmv_matrix *h, BatchMat &M) {
+    M.fmt = SPMV_FMT_CSR;
+    if (h->cfg.format == SPMV_FMT_ELL && (h->ell_col || h->ell_d16)) {
+        M.fmt = SPMV_FMT_ELL;
+        M.ell_col = h->ell_col;
+        M.ell_d16 = h->ell_d16;
+        M.ell_val = h->ell_val;
+        M.ell_width = h->ell_width;
+        M.ell_pitch = h->ell_pitch;
+    } else if (h->cfg.format == SPMV_FMT_SELL && h->sell_col) {
+        const LongRows &L = h->lng;
+        M.fmt = SPMV_FMT_SELL;
+        M.it_slice = L.seg_row;
+        M.it_base = L.seg_begin;
+        M.it_len = L.seg_end;
+        M.it_c0 = L.seg_c0;
+        M.it_c1 = L.seg_c1;
+        M.sell_col = h->sell_col;
+        M.sell_perm = h->sell_perm;
+        M.sell_val = h->sell_val;
+        M.nitems = L.nseg;
+        M.s_zero = L.nrows;
+        M.p_head = L.part.head;
+        M.p_tail = L.part.tail;
+        M.p_count = L.part.count;
+        M.p_xslot = L.part.xslot;
+    }
+}
 
 template <typename V, typename T, int ITEMS>
 __global__ void __launch_bounds__(512)
@@ -72,7 +127,24 @@ k_batch(const BatchMat *__restrict__ mats, int count, const int64_t *__restrict_
         const V *vals = (const V *)M.vals;
         const T *x = (const T *)M.x;
         T *y = (T *)M.y;
-        if (M.mode == 0) {
+        if (M.fmt == SPMV_FMT_ELL) {  // 32 rows, one per lane
+            const int64_t r = local * 32 + lane;
+            if (r < M.m) {
+                if (M.ell_d16)
+                    ell_row<V, T, 4, int16_t>(r, M.ell_width, M.ell_pitch, M.ell_d16, (const V *)M.ell_val, x, y, ep);
+                else
+                    ell_row<V, T, 4, int>(r, M.ell_width, M.ell_pitch, M.ell_col, (const V *)M.ell_val, x, y, ep);
+            }
+        } else if (M.fmt == SPMV_FMT_SELL) {
+            if (local < M.nitems) {
+                const PartialsT<T> Ps{(T *)M.p_head, (T *)M.p_tail, M.p_count, M.p_xslot, 32};
+                sell_item<V, T, 4>(local, M.m, M.it_slice, M.it_base, M.it_len, M.it_c0, M.it_c1, M.sell_col,
+                                   (const V *)M.sell_val, M.sell_perm, x, y, ep, Ps);
+            } else {  // 32 of the empty rows
+                const int64_t p = M.s_zero * 32 + (local - M.nitems) * 32 + lane;
+                if (p < M.m) ep.store(y, __ldg(M.sell_perm + p), T(0));
+            }
+        } else if (M.mode == 0) {
             PartialsT<T> Pm = P;
             Pm.head += M.part_off;
             Pm.tail += M.part_off;
@@ -179,20 +251,16 @@ int build(spmv_batch *b, cudaStream_t s) {
         M.mode = b->modes[i];
         M.part_off = 0;
         M.meta0 = nullptr;
-        M.pad = 0;
-        int64_t items;
-        if (M.mode == 0) {
+        describe_format(h, M);
+        if (M.fmt == SPMV_FMT_CSR && M.mode == 0) {
             const int64_t nch = (h->nnz + C - 1) / C;
             SPMV_CUDA_TRY(dev_malloc((void **)&b->metas[i], sizeof(int32_t) * (nch + 1)));
             SPMV_TRY(build_split_meta(h->rowptr, h->m, h->nnz, C, b->metas[i], s));
             M.meta0 = b->metas[i];
             M.part_off = chunks_total;
             chunks_total += nch;
-            items = nch;
-        } else {
-            items = (h->m + 31) / 32;
         }
-        off[i + 1] = off[i] + items;
+        off[i + 1] = off[i] + batch_items(M, C);
     }
     b->total_items = off[b->count];
     SPMV_TRY(alloc_partials(&b->part, chunks_total, 1, b->vt, s));
@@ -289,7 +357,13 @@ int spmv_batch_create(spmv_batch_handle *out, const spmv_handle *hs, int32_t cou
     b->x.assign(d_x, d_x + count);
     b->y.assign(d_y, d_y + count);
     b->modes.resize(count);
-    for (int i = 0; i < count; ++i) b->modes[i] = default_mode(hs[i]);
+    for (int i = 0; i < count; ++i) {
+        BatchMat probe{};
+        describe_format(hs[i], probe);
+        // ELL and SELL matrices run in their own format (mode -format); the
+        // others in a CSR mode
+        b->modes[i] = probe.fmt == SPMV_FMT_CSR ? default_mode(hs[i]) : -probe.fmt;
+    }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev);
@@ -330,6 +404,11 @@ int spmv_batch_tune(spmv_batch_handle b, void *stream) {
     for (int i = 0; i < b->count; ++i) {
         const spmv_matrix *h = b->hs[i];
         if (h->m == 0) continue;
+        {
+            BatchMat probe{};
+            describe_format(h, probe);
+            if (probe.fmt != SPMV_FMT_CSR) continue;  // ELL and SELL matrices run their own kernel bodies
+        }
         int best_mode = b->modes[i];
         float best_t = 1e30f;
         for (int mode : cand) {
@@ -351,8 +430,18 @@ int spmv_batch_tune(spmv_batch_handle b, void *stream) {
             one.cs = b->cs;
             // build descriptors without capturing a graph
             const int C = 32 * one.items;
-            BatchMat M{h->rowptr, h->colidx, h->vals, b->x[i], b->y[i], b->alpha[i], b->beta[i], h->m, h->nnz, 0,
-                       nullptr, mode, 0};
+            BatchMat M{};
+            M.rowptr = h->rowptr;
+            M.colidx = h->colidx;
+            M.vals = h->vals;
+            M.x = b->x[i];
+            M.y = b->y[i];
+            M.alpha = b->alpha[i];
+            M.beta = b->beta[i];
+            M.m = h->m;
+            M.nnz = h->nnz;
+            M.mode = mode;
+            M.fmt = SPMV_FMT_CSR;
             int64_t off[2] = {0, mode == 0 ? (h->nnz + C - 1) / C : (h->m + 31) / 32};
             int32_t *meta = nullptr;
             BatchMat *d_m = nullptr;

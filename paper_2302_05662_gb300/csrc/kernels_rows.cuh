@@ -137,41 +137,48 @@ __device__ __forceinline__ int ell_col_at(const int16_t *p, int64_t r) {
     return d == INT16_MIN ? -1 : (int)r + d;
 }
 
+// One ELL row r (thread per row), shared by k_ell and the batched kernel.
+template <typename V, typename T, int UNROLL, typename CI>
+__device__ __forceinline__ void ell_row(int64_t r, int64_t width, int64_t pitch, const CI *__restrict__ col,
+                                        const V *__restrict__ val, const T *__restrict__ x, T *__restrict__ y,
+                                        const Epi<T> &ep) {
+    T acc = T(0);
+    int64_t k = 0;
+    bool done = false;
+    for (; !done && k + UNROLL <= width; k += UNROLL) {
+        // all loads of the group go out together: padding slots hold a
+        // zero value and column -1 (gathered at column 0, not added)
+        int c[UNROLL];
+        T v[UNROLL], xv[UNROLL];
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) c[u] = ell_col_at(col + (k + u) * pitch + r, r);
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) {
+            v[u] = ld_val(val + (k + u) * pitch + r);
+            xv[u] = ld_x(x, c[u] >= 0 ? c[u] : 0);
+        }
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) {
+            if (c[u] >= 0) acc = fma(v[u], xv[u], acc);
+            else done = true;
+        }
+    }
+    for (; !done && k < width; ++k) {
+        const int c = ell_col_at(col + k * pitch + r, r);
+        if (c < 0) break;
+        acc += ld_val(val + k * pitch + r) * ld_x(x, c);
+    }
+    ep.store(y, r, acc);
+}
+
 template <typename V, typename T, int UNROLL, int REGCAP, typename CI>
 __global__ void __launch_bounds__(1024) __maxnreg__(REGCAP)
 k_ell(int64_t m, int64_t width, int64_t pitch, const CI *__restrict__ col, const V *__restrict__ val,
       const T *__restrict__ x, T *__restrict__ y, T alpha, T beta) {
     const Epi<T> ep(alpha, beta);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < m; r += stride) {
-        T acc = T(0);
-        int64_t k = 0;
-        bool done = false;
-        for (; !done && k + UNROLL <= width; k += UNROLL) {
-            // all loads of the group go out together: padding slots hold a
-            // zero value and column -1 (gathered at column 0, not added)
-            int c[UNROLL];
-            T v[UNROLL], xv[UNROLL];
-#pragma unroll
-            for (int u = 0; u < UNROLL; ++u) c[u] = ell_col_at(col + (k + u) * pitch + r, r);
-#pragma unroll
-            for (int u = 0; u < UNROLL; ++u) {
-                v[u] = ld_val(val + (k + u) * pitch + r);
-                xv[u] = ld_x(x, c[u] >= 0 ? c[u] : 0);
-            }
-#pragma unroll
-            for (int u = 0; u < UNROLL; ++u) {
-                if (c[u] >= 0) acc = fma(v[u], xv[u], acc);
-                else done = true;
-            }
-        }
-        for (; !done && k < width; ++k) {
-            const int c = ell_col_at(col + k * pitch + r, r);
-            if (c < 0) break;
-            acc += ld_val(val + k * pitch + r) * ld_x(x, c);
-        }
-        ep.store(y, r, acc);
-    }
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < m; r += stride)
+        ell_row<V, T, UNROLL, CI>(r, width, pitch, col, val, x, y, ep);
 }
 
 // Two adjacent rows per thread (fp32/bf16 values): rows r, r + 1 sit side by
@@ -388,6 +395,50 @@ k_bsr_long(int64_t nseg, const int *__restrict__ seg_row, const int *__restrict_
 // per-row partials are joined in item order, so a slice of power-law rows is
 // not left to one warp.  Slices of empty rows get no work item.
 // ---------------------------------------------------------------------------
+// Work item `it` of a SELL matrix (the whole warp), shared by k_sell and the
+// batched kernel.
+template <typename V, typename T, int UNROLL>
+__device__ __forceinline__ void sell_item(int64_t it, int64_t m, const int *__restrict__ it_slice,
+                                          const int *__restrict__ it_base, const int *__restrict__ it_len,
+                                          const int *__restrict__ it_c0, const int *__restrict__ it_c1,
+                                          const int *__restrict__ col, const V *__restrict__ val,
+                                          const int *__restrict__ perm, const T *__restrict__ x, T *__restrict__ y,
+                                          const Epi<T> &ep, const PartialsT<T> &P) {
+    const int lane = threadIdx.x & 31;
+    // an item is three independent loads: slice, slot offset, columns;
+    // the row this lane writes and the item's join range are requested
+    // with them, so their latency overlaps the item's loads
+    const int sl = __ldg(it_slice + it), ib = __ldg(it_base + it), len = __ldg(it_len + it);
+    const int64_t c0 = __ldg(it_c0 + it), c1 = __ldg(it_c1 + it);
+    const int64_t p = (int64_t)sl * 32 + lane;
+    const int row = p < m ? __ldg(perm + p) : -1;
+    const int64_t base = (int64_t)ib + lane;
+    T acc = T(0);
+    int k = 0;
+    for (; k + UNROLL <= len; k += UNROLL) {
+        int c[UNROLL];
+        T v[UNROLL], xv[UNROLL];
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) c[u] = ld_s(col + base + 32LL * (k + u));
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) {
+            v[u] = ld_val(val + base + 32LL * (k + u));
+            xv[u] = ld_x(x, c[u] >= 0 ? c[u] : 0);
+        }
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u)
+            if (c[u] >= 0) acc = fma(v[u], xv[u], acc);
+    }
+    for (; k < len; ++k) {
+        const int c = ld_s(col + base + 32LL * k);
+        if (c >= 0) acc = fma(ld_val(val + base + 32LL * k), ld_x(x, c), acc);
+    }
+    if (p < m) {
+        T total = acc;
+        if (c0 == c1 || join_partial<T>(it, c0, c1, lane, acc, P, &total)) ep.store(y, row, total);
+    }
+}
+
 template <typename V, typename T, int UNROLL, int REGCAP>
 __global__ void __launch_bounds__(1024) __maxnreg__(REGCAP)
 k_sell(int64_t m, int64_t nitems, int64_t s_zero, const int *__restrict__ it_slice, const int *__restrict__ it_base,
@@ -395,7 +446,6 @@ k_sell(int64_t m, int64_t nitems, int64_t s_zero, const int *__restrict__ it_sli
        const int *__restrict__ col, const V *__restrict__ val, const int *__restrict__ perm,
        const T *__restrict__ x, T *__restrict__ y, T alpha, T beta, const PartialsT<T> P) {
     const Epi<T> ep(alpha, beta);
-    const int lane = threadIdx.x & 31;
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t warp = gtid >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -409,38 +459,7 @@ k_sell(int64_t m, int64_t nitems, int64_t s_zero, const int *__restrict__ it_sli
     for (int64_t j = 0; j * nwarps < nitems; ++j) {
         const int64_t it = j * nwarps + ((j & 1) ? nwarps - 1 - warp : warp);
         if (it >= nitems) continue;
-        // an item is three independent loads: slice, slot offset, columns;
-        // the row this lane writes and the item's join range are requested
-        // with them, so their latency overlaps the item's loads
-        const int sl = __ldg(it_slice + it), ib = __ldg(it_base + it), len = __ldg(it_len + it);
-        const int64_t c0 = __ldg(it_c0 + it), c1 = __ldg(it_c1 + it);
-        const int64_t p = (int64_t)sl * 32 + lane;
-        const int row = p < m ? __ldg(perm + p) : -1;
-        const int64_t base = (int64_t)ib + lane;
-        T acc = T(0);
-        int k = 0;
-        for (; k + UNROLL <= len; k += UNROLL) {
-            int c[UNROLL];
-            T v[UNROLL], xv[UNROLL];
-#pragma unroll
-            for (int u = 0; u < UNROLL; ++u) c[u] = ld_s(col + base + 32LL * (k + u));
-#pragma unroll
-            for (int u = 0; u < UNROLL; ++u) {
-                v[u] = ld_val(val + base + 32LL * (k + u));
-                xv[u] = ld_x(x, c[u] >= 0 ? c[u] : 0);
-            }
-#pragma unroll
-            for (int u = 0; u < UNROLL; ++u)
-                if (c[u] >= 0) acc = fma(v[u], xv[u], acc);
-        }
-        for (; k < len; ++k) {
-            const int c = ld_s(col + base + 32LL * k);
-            if (c >= 0) acc = fma(ld_val(val + base + 32LL * k), ld_x(x, c), acc);
-        }
-        if (p < m) {
-            T total = acc;
-            if (c0 == c1 || join_partial<T>(it, c0, c1, lane, acc, P, &total)) ep.store(y, row, total);
-        }
+        sell_item<V, T, UNROLL>(it, m, it_slice, it_base, it_len, it_c0, it_c1, col, val, perm, x, y, ep, P);
     }
 }
 

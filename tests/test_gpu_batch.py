@@ -156,3 +156,53 @@ def test_batch_fullsize_512_fp32_tuned(oracle):
     finally:
         for h in hs:
             B.spmv_destroy(h)
+
+
+FORMAT_CYCLE = [B.FMT_ELL, B.FMT_SELL, B.FMT_CSR, B.FMT_COO, B.FMT_HYB, B.FMT_BSR]
+
+
+@pytest.mark.parametrize("vt", [B.SPMV_F32, B.SPMV_F64, B.SPMV_BF16])
+def test_batch_runs_each_matrix_in_its_format(oracle, vt):
+    """Handles in ELL and SELL run in their own format inside the batch
+    (modes -1 and -5), the others from their CSR arrays; every product
+    matches the oracle before and after the autotuner."""
+    import torch
+    mats = batch_matrices(count=36, seed=3)
+    hs, xs, ys, xh = [], [], [], []
+    want_modes = []
+    for i, coo in enumerate(mats):
+        h = create(coo, vt)
+        fmt = FORMAT_CYCLE[i % len(FORMAT_CYCLE)]
+        try:
+            B.spmv_set_config(h, B.make_config(format=fmt))
+        except B.SpmvError:
+            fmt = B.FMT_CSR                      # a padded format over its limit: the handle stays CSR
+        hs.append(h)
+        want_modes.append(-fmt if fmt in (B.FMT_ELL, B.FMT_SELL) else None)
+        x = matgen.dense_vector(coo.n, 70 + i)
+        xh.append(x)
+        xs.append(torch.from_numpy(x).to(vec_dtype(vt)).cuda())
+        ys.append(torch.full((coo.m,), float("nan"), dtype=vec_dtype(vt), device="cuda"))
+    ones, zeros = np.ones(len(mats)), np.zeros(len(mats))
+    b = B.spmv_batch_create(hs, ones, xs, zeros, ys)
+    try:
+        modes, _, _ = B.spmv_batch_get_plan(b, len(mats))
+        for i, wm in enumerate(want_modes):
+            if wm is not None and mats[i].m > 0:
+                assert modes[i] == wm, i
+            elif wm is None:
+                assert modes[i] >= 0, i
+        for tuned in (False, True):
+            if tuned:
+                B.spmv_batch_tune(b)
+            for y in ys:
+                y.fill_(float("nan"))
+            B.spmv_batch_launch(b)
+            torch.cuda.synchronize()
+            for i, coo in enumerate(mats):
+                want = oracle_for(oracle, coo, vt, xh[i])
+                assert rel_err(ys[i].cpu().double().numpy(), want) <= TOL[vt], (tuned, i)
+    finally:
+        B.spmv_batch_destroy(b)
+        for h in hs:
+            B.spmv_destroy(h)
