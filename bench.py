@@ -70,6 +70,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--only", default=None, help="comma-separated matrix names (profiling runs)")
     p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--batched-only", type=int, default=None, metavar="COUNT",
+                   help="profiling runs: only the batched section, over COUNT matrices, then exit")
     p.add_argument("--mode", default="replicas", choices=["replicas", "shard"],
                    help="N > 1: independent replicas of the step (weak scaling), or every product sharded "
                         "by nnz-balanced row blocks with an all-gather of x (strong scaling)")
@@ -407,7 +409,9 @@ def batched_section(B, matgen, torch, count=512, seed=7, steps=20, select=True):
             torch.cuda.synchronize()
             return e0.elapsed_time(e1) / steps
 
+        torch.cuda.nvtx.range_push("batched_graph")    # ncu --nvtx-include "batched_graph/"
         t_graph = timed(lambda: B.spmv_batch_launch(b, sh))
+        torch.cuda.nvtx.range_pop()
 
         def separate():
             for k in range(count):
@@ -579,6 +583,10 @@ def ours(args, world, rank, local):
         S.load_default_selector()
     if args.no_tune and not have_selector:
         raise SystemExit("--no-tune needs the trained selector")
+    if args.batched_only:
+        if rank == 0:
+            print(json.dumps({"batched": batched_section(B, matgen, torch, count=args.batched_only)}), flush=True)
+        return
     timer = sweep.Timer()
 
     only = set(args.only.split(",")) if args.only else None

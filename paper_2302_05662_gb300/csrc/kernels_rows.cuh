@@ -22,7 +22,62 @@ constexpr unsigned FULLMASK = 0xffffffffu;
 // long_threshold are left to k_csr_long.  All loops are warp-uniform, so the
 // shuffle reduction always has every lane.
 // ---------------------------------------------------------------------------
+// 4 stored values starting at a multiple of 4 entries, L1-allocating (a
+// lane walks its own row: the group after this one sits in the same sector)
+__device__ __forceinline__ void ld_vals4_c(const double *p, double (&o)[4]) {
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+    const double2 b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+__device__ __forceinline__ void ld_vals4_c(const float *p, float (&o)[4]) {
+    const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+}
+__device__ __forceinline__ void ld_vals4_c(const __nv_bfloat16 *p, float (&o)[4]) {
+    const uint2 w = __ldg(reinterpret_cast<const uint2 *>(p));
+    o[0] = bf16lo(w.x); o[1] = bf16hi(w.x); o[2] = bf16lo(w.y); o[3] = bf16hi(w.y);
+}
+
+// Entries [a, b) of one row summed by one lane with 16-byte loads: the lane
+// walks the aligned groups of 4 entries covering its range (the first and
+// last group masked), G groups in flight.  The column and value arrays are
+// padded past nnz, so the last group's load stays inside them.
+template <typename V, typename T, int G>
+__device__ __forceinline__ T csr_lane_range(int a, int b, const int *__restrict__ colidx, const V *__restrict__ vals,
+                                            const T *__restrict__ x) {
+    T acc = T(0);
+    for (int q = a & ~3; q < b; q += 4 * G) {
+        int c[G][4];
+        T v[G][4], xv[G][4];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const int gq = q + 4 * g;
+            if (gq < b) {
+                const int4 w = __ldg(reinterpret_cast<const int4 *>(colidx + gq));
+                c[g][0] = w.x; c[g][1] = w.y; c[g][2] = w.z; c[g][3] = w.w;
+                ld_vals4_c(vals + gq, v[g]);
+            }
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                if (gq >= b || gq + t < a || gq + t >= b) c[g][t] = -1;
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+#pragma unroll
+            for (int t = 0; t < 4; ++t) xv[g][t] = c[g][t] >= 0 ? ld_x(x, c[g][t]) : T(0);
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                if (c[g][t] >= 0) acc = fma(v[g][t], xv[g][t], acc);
+    }
+    return acc;
+}
+
 // Rows [base, base + 32) with TPR lanes per row; the whole warp calls it.
+// With one or two lanes per row each lane sums a contiguous part of its row
+// with 16-byte loads (csr_lane_range); with more lanes, the lanes of a row
+// take interleaved entries, so a warp's loads of a row are contiguous.
 template <typename V, typename T, int TPR, int UNROLL>
 __device__ __forceinline__ void csr_vector_rows(int64_t base, int64_t m, const int *__restrict__ rowptr,
                                                 const int *__restrict__ colidx, const V *__restrict__ vals,
@@ -42,20 +97,23 @@ __device__ __forceinline__ void csr_vector_rows(int64_t base, int64_t m, const i
         const int64_t row = base + src;
         const bool skip = row >= m || e - s > long_threshold;
         T acc = T(0);
-        if (!skip) {
+        if constexpr (TPR <= 2) {
+            if (!skip) {
+                // lane sub takes [s, mid) or [mid, e), mid on a 4-entry boundary
+                int mid = TPR == 1 ? e : ((s + (e - s) / 2 + 3) & ~3);
+                mid = mid < s ? s : (mid > e ? e : mid);
+                const int a = sub == 0 ? s : mid, b = sub == 0 ? mid : e;
+                acc = csr_lane_range<V, T, (UNROLL >= 4 ? 2 : 1)>(a, b, colidx, vals, x);
+            }
+        } else if (!skip) {
             for (int k = s + sub; k < e; k += TPR * UNROLL) {
                 int c[UNROLL];
                 T v[UNROLL];
 #pragma unroll
                 for (int u = 0; u < UNROLL; ++u) {
                     const int kk = k + u * TPR;
-                    if constexpr (TPR <= 2) {  // lanes walk their own rows: keep lines in L1
-                        c[u] = kk < e ? __ldg(colidx + kk) : -1;
-                        v[u] = kk < e ? ld_val_c(vals + kk) : T(0);
-                    } else {
-                        c[u] = kk < e ? ld_s(colidx + kk) : -1;
-                        v[u] = kk < e ? ld_val(vals + kk) : T(0);
-                    }
+                    c[u] = kk < e ? ld_s(colidx + kk) : -1;
+                    v[u] = kk < e ? ld_val(vals + kk) : T(0);
                 }
 #pragma unroll
                 for (int u = 0; u < UNROLL; ++u)

@@ -398,7 +398,10 @@ def main():
     ap.add_argument("--from-blob", default=None, help="reuse this blob's classifier, fit only the heads")
     ap.add_argument("--calib", nargs="*", default=None, help="conversion-time records (JSON lines)")
     ap.add_argument("--refine", nargs="*", default=None,
-                    help="refine records (sweep --refine-from): per-class register cap, unroll and carveout")
+                    help="refine records (sweep --refine-from): evaluate a per-class register cap / unroll / "
+                         "carveout table against the refined exhaustive best")
+    ap.add_argument("--apply-knobs", action="store_true",
+                    help="write the per-class knob table into the blob's labels (default: report only)")
     args = ap.parse_args()
     recs = load_records(args.data)
     labels = sweep.label_space(include_sell=has_sell(recs))
@@ -478,9 +481,11 @@ def main():
     if args.refine:
         refine = load_refine(args.refine)
         table = knob_table(refine, ids[train_m])
-        labels = [dict(c, **dict(zip(KNOBS, table[keys[j]]))) if keys[j] in table else c
-                  for j, c in enumerate(labels)]
+        if args.apply_knobs:
+            labels = [dict(c, **dict(zip(KNOBS, table[keys[j]]))) if keys[j] in table else c
+                      for j, c in enumerate(labels)]
         report["knob_table"] = {k: dict(zip(KNOBS, v)) for k, v in sorted(table.items())}
+        report["knob_table_applied"] = bool(args.apply_knobs)
         for name, msk in (("train", train_m), ("heldout", test_m)):
             logits = np.where(np.isfinite(T[msk]), predict(w, X[msk]), -np.inf)
             choice = np.argmax(logits, axis=1)
