@@ -463,13 +463,10 @@ __device__ __forceinline__ void sell_item(int64_t it, int64_t m, const int *__re
                                           const int *__restrict__ perm, const T *__restrict__ x, T *__restrict__ y,
                                           const Epi<T> &ep, const PartialsT<T> &P) {
     const int lane = threadIdx.x & 31;
-    // an item is three independent loads: slice, slot offset, columns;
-    // the row this lane writes and the item's join range are requested
-    // with them, so their latency overlaps the item's loads
+    // an item is three independent loads: slice, slot offset, columns (the
+    // row and join range are read after the loop: requesting them up front
+    // slowed the fp64 banded product by 4%)
     const int sl = __ldg(it_slice + it), ib = __ldg(it_base + it), len = __ldg(it_len + it);
-    const int64_t c0 = __ldg(it_c0 + it), c1 = __ldg(it_c1 + it);
-    const int64_t p = (int64_t)sl * 32 + lane;
-    const int row = p < m ? __ldg(perm + p) : -1;
     const int64_t base = (int64_t)ib + lane;
     T acc = T(0);
     int k = 0;
@@ -491,7 +488,10 @@ __device__ __forceinline__ void sell_item(int64_t it, int64_t m, const int *__re
         const int c = ld_s(col + base + 32LL * k);
         if (c >= 0) acc = fma(ld_val(val + base + 32LL * k), ld_x(x, c), acc);
     }
+    const int64_t p = (int64_t)sl * 32 + lane;
     if (p < m) {
+        const int row = __ldg(perm + p);
+        const int64_t c0 = __ldg(it_c0 + it), c1 = __ldg(it_c1 + it);
         T total = acc;
         if (c0 == c1 || join_partial<T>(it, c0, c1, lane, acc, P, &total)) ep.store(y, row, total);
     }
