@@ -121,12 +121,17 @@ typedef enum {
  *   carveout          preferred shared-memory carveout in percent (0..100),
  *                     or -1 to leave the driver default (Section 4 item 3).
  *                     Zero means 0 % (maximum L1), not "default".
- *   bsr_block         BSR block size r: 2 or 4 (default 4).
+ *   bsr_block         BSR block size r: 2 or 4 (default 4).  SELL: column
+ *                     groups, 4 (a lane's four entries of four consecutive
+ *                     columns side by side: 16-byte loads) or 1 (column-
+ *                     major); 0 = 4 unless the longest row exceeds 32 mean
+ *                     rows plus 32 (power-law rows: mostly narrow slices,
+ *                     where column-major runs faster), then 1.
  *   hyb_ell_width     HYB ELL width; 0 applies the width rule (the largest
  *                     k such that at least max(4096, m/3) rows hold k or
  *                     more nonzeros).  SELL: columns of a slice per work
- *                     item, 8..65536 (0 = 128); wider slices are split into
- *                     several items joined in order.  CSR with
+ *                     item, a multiple of 4 in 8..65536 (0 = 128); wider
+ *                     slices are split into several items joined in order.  CSR with
  *                     SPMV_TPR_SPLIT: nonzeros per tile staged through
  *                     shared memory, a multiple of 256 in [256, 8192]
  *                     (0 = 4096).
@@ -231,8 +236,10 @@ typedef enum {
     SPMV_ARR_BSR_VALS = 10,   /* value_type[blocks][r][r], row-major blocks  */
     SPMV_ARR_ELL_PITCH = 11,  /* (size query only) pitch in elements          */
     SPMV_ARR_SELL_PTR = 12,   /* int32[slices+1]: first slot of each slice     */
-    SPMV_ARR_SELL_COLIDX = 13,/* int32[slots]: slice s, entry k, lane l at     */
-                              /* ptr[s] + 32 k + l; -1 = padding               */
+    SPMV_ARR_SELL_COLIDX = 13,/* int32[slots]: slice s of width w, entry k,    */
+                              /* lane l at ptr[s] + 128 (k/4) + 4 l + k%4 for  */
+                              /* k < (w & ~3), else at ptr[s] + 32 (w & ~3) +   */
+                              /* 32 (k - (w & ~3)) + l; -1 = padding            */
     SPMV_ARR_SELL_VALS = 14,  /* value_type[slots], 0 = padding                */
     SPMV_ARR_SELL_PERM = 15   /* int32[m]: matrix row held by sorted row p     */
                               /* (rows sorted by descending length, stable)    */

@@ -149,7 +149,13 @@ int resolve_config(const spmv_matrix *h, const spmv_config *in, spmv_config *out
     if (c.threads_per_block == 0) c.threads_per_block = 256;
     if (c.unroll == 0) c.unroll = default_unroll(c.format, h->vt);
     if (c.regcap == 0) c.regcap = default_regcap(c.format, h->vt);
-    if (c.bsr_block == 0) c.bsr_block = 4;
+    if (c.bsr_block == 0) {
+        // SELL: groups of four columns unless the rows follow a power law
+        // (a longest row beyond 32 mean rows: there most slices are a few
+        // columns wide and column-major runs faster); BSR: 4 x 4 blocks
+        const double mean = h->m > 0 ? (double)h->nnz / (double)h->m : 0.0;
+        c.bsr_block = c.format == SPMV_FMT_SELL && (double)h->max_row > 32.0 * mean + 32.0 ? 1 : 4;
+    }
     if (c.format < SPMV_FMT_CSR || c.format > SPMV_FMT_SELL) {
         set_error("config: unknown format %d", c.format);
         return SPMV_ERR_INVALID;
@@ -171,8 +177,8 @@ int resolve_config(const spmv_matrix *h, const spmv_config *in, spmv_config *out
         set_error("config: carveout %d not in [-1, 100]", c.carveout);
         return SPMV_ERR_INVALID;
     }
-    if (c.bsr_block != 2 && c.bsr_block != 4) {
-        set_error("config: bsr_block %d not in {2, 4}", c.bsr_block);
+    if (c.format == SPMV_FMT_SELL ? (c.bsr_block != 1 && c.bsr_block != 4) : (c.bsr_block != 2 && c.bsr_block != 4)) {
+        set_error("config: bsr_block %d not in {2, 4} ({1, 4} for SELL column groups)", c.bsr_block);
         return SPMV_ERR_INVALID;
     }
     if (c.hyb_ell_width < 0) {
@@ -183,8 +189,8 @@ int resolve_config(const spmv_matrix *h, const spmv_config *in, spmv_config *out
         // 128 balances warps best on power-law rows (R-MAT scale 20, fp64:
         // 80.6 us at 128, 86.7 at 256, 95.9 at 64, 197 at 1024)
         if (c.hyb_ell_width == 0) c.hyb_ell_width = 128;
-        if (c.hyb_ell_width < 8 || c.hyb_ell_width > 65536) {
-            set_error("config: SELL columns per work item %d not in [8, 65536]", c.hyb_ell_width);
+        if (c.hyb_ell_width < 8 || c.hyb_ell_width > 65536 || c.hyb_ell_width % 4 != 0) {
+            set_error("config: SELL columns per work item %d not a multiple of 4 in [8, 65536]", c.hyb_ell_width);
             return SPMV_ERR_INVALID;
         }
     }
@@ -351,7 +357,7 @@ void spmv_config_default(spmv_config *cfg, int32_t format) {
     cfg->unroll = 0;  // per format and value type, resolved when applied
     cfg->regcap = 0;
     cfg->carveout = -1;
-    cfg->bsr_block = 4;
+    cfg->bsr_block = format == SPMV_FMT_SELL ? 0 : 4;  // SELL: column groups chosen per matrix
     cfg->hyb_ell_width = 0;
 }
 

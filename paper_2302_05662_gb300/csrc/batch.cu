@@ -63,6 +63,7 @@ struct BatchMat {
     const int *sell_col, *sell_perm;
     const void *sell_val;
     int64_t nitems, s_zero;
+    int sell_grouped, pad2;
     void *p_head, *p_tail;
     unsigned *p_count;
     unsigned long long *p_xslot;
@@ -99,6 +100,7 @@ void describe_format(const spmv_matrix *h, BatchMat &M) {
         M.sell_val = h->sell_val;
         M.nitems = L.nseg;
         M.s_zero = L.nrows;
+        M.sell_grouped = h->sell_grouped ? 1 : 0;
         M.p_head = L.part.head;
         M.p_tail = L.part.tail;
         M.p_count = L.part.count;
@@ -138,8 +140,12 @@ k_batch(const BatchMat *__restrict__ mats, int count, const int64_t *__restrict_
         } else if (M.fmt == SPMV_FMT_SELL) {
             if (local < M.nitems) {
                 const PartialsT<T> Ps{(T *)M.p_head, (T *)M.p_tail, M.p_count, M.p_xslot, 32};
-                sell_item<V, T, 4>(local, M.m, M.it_slice, M.it_base, M.it_len, M.it_c0, M.it_c1, M.sell_col,
-                                   (const V *)M.sell_val, M.sell_perm, x, y, ep, Ps);
+                if (M.sell_grouped)
+                    sell_item<V, T, 8, true>(local, M.m, M.it_slice, M.it_base, M.it_len, M.it_c0, M.it_c1,
+                                             M.sell_col, (const V *)M.sell_val, M.sell_perm, x, y, ep, Ps);
+                else
+                    sell_item<V, T, 4, false>(local, M.m, M.it_slice, M.it_base, M.it_len, M.it_c0, M.it_c1,
+                                              M.sell_col, (const V *)M.sell_val, M.sell_perm, x, y, ep, Ps);
             } else {  // 32 of the empty rows
                 const int64_t p = M.s_zero * 32 + (local - M.nitems) * 32 + lane;
                 if (p < M.m) ep.store(y, __ldg(M.sell_perm + p), T(0));

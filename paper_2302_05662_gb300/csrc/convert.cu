@@ -574,12 +574,23 @@ __global__ void k_sell_widths(const int *rowptr, const uint32_t *perm, int64_t m
     }
 }
 
-// one warp per 32-slot column (slice sl, entry k) of the layout: slots of a
-// slice come in multiples of 32, so the warp finds (sl, k) with one binary
-// search (same address in every lane) and lane l fills sorted row 32 sl + l
+// Slot of entry k of lane l in a slice of width w starting at slot base:
+// the first w & ~3 columns in groups of four, each group 32 lanes x 4
+// consecutive entries (a lane's four entries of a group contiguous), then
+// the remaining w & 3 columns column-major (32 lanes each).
+// (grouped = false: every column column-major, entry k at base + 32 k + l)
+__host__ __device__ __forceinline__ int64_t sell_slot(int64_t base, int64_t w, int64_t k, int l, bool grouped) {
+    const int64_t w4 = grouped ? (w & ~int64_t(3)) : 0;
+    return k < w4 ? base + 128 * (k >> 2) + 4 * l + (k & 3) : base + 32 * w4 + 32 * (k - w4) + l;
+}
+
+// one warp per entry index k of a slice (slices hold 32 slots per column,
+// so the warp finds (sl, k) from its 32-slot index with one binary search,
+// the same address in every lane) and lane l fills sorted row 32 sl + l
 template <typename V>
 __global__ void k_sell_fill(const int *rowptr, const int *colidx, const V *vals, const uint32_t *perm, int64_t m,
-                            int64_t nslices, const int *sptr, int64_t total, int *scol, V *sval, int *sperm) {
+                            int64_t nslices, const int *sptr, int64_t total, int *scol, V *sval, int *sperm,
+                            bool grouped) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -598,8 +609,9 @@ __global__ void k_sell_fill(const int *rowptr, const int *colidx, const V *vals,
                 v = vals[rs + k];
             }
         }
-        scol[p0 + lane] = c;
-        sval[p0 + lane] = v;
+        const int64_t at = sell_slot(sptr[sl], (sptr[sl + 1] - sptr[sl]) / 32, k, lane, grouped);
+        scol[at] = c;
+        sval[at] = v;
     }
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < m; q += stride) sperm[q] = (int)perm[q];
@@ -1209,11 +1221,12 @@ int pack_bsr(spmv_matrix *h, int r, cudaStream_t s) {
 namespace {
 
 // kmax: columns of a slice per work item (wider slices become several items)
-int pack_sell(spmv_matrix *h, int kmax, cudaStream_t s) {
+int pack_sell(spmv_matrix *h, int kmax, bool grouped, cudaStream_t s) {
     const int64_t m = h->m;
     const int64_t nslices = (m + 31) / 32;
     const size_t vs = value_size(h->vt);
     h->sell_nslices = nslices;
+    h->sell_grouped = grouped;
     SPMV_TRY(dalloc(&h->sell_ptr, (size_t)nslices + 1));
     SPMV_TRY(dalloc(&h->sell_perm, (size_t)std::max<int64_t>(m, 1)));
     if (m == 0) {
@@ -1251,14 +1264,16 @@ int pack_sell(spmv_matrix *h, int kmax, cudaStream_t s) {
     const unsigned g = grid1d(std::max<int64_t>(total, m), 256);
     if (h->vt == SPMV_F64)
         k_sell_fill<double><<<g, 256, 0, s>>>(h->rowptr, h->colidx, (const double *)h->vals, perm, m, nslices,
-                                              h->sell_ptr, total, h->sell_col, (double *)h->sell_val, h->sell_perm);
+                                              h->sell_ptr, total, h->sell_col, (double *)h->sell_val, h->sell_perm,
+                                              grouped);
     else if (h->vt == SPMV_F32)
         k_sell_fill<float><<<g, 256, 0, s>>>(h->rowptr, h->colidx, (const float *)h->vals, perm, m, nslices,
-                                             h->sell_ptr, total, h->sell_col, (float *)h->sell_val, h->sell_perm);
+                                             h->sell_ptr, total, h->sell_col, (float *)h->sell_val, h->sell_perm,
+                                             grouped);
     else
         k_sell_fill<__nv_bfloat16><<<g, 256, 0, s>>>(h->rowptr, h->colidx, (const __nv_bfloat16 *)h->vals, perm, m,
                                                      nslices, h->sell_ptr, total, h->sell_col,
-                                                     (__nv_bfloat16 *)h->sell_val, h->sell_perm);
+                                                     (__nv_bfloat16 *)h->sell_val, h->sell_perm, grouped);
     SPMV_CUDA_TRY(cudaGetLastError());
     // work items (slice, first slot, column count <= 256) and the partials
     // joining the items of one slice
@@ -1384,7 +1399,7 @@ int pack_format(spmv_matrix *h, const spmv_config &cfg, cudaStream_t s) {
         break;
     }
     case SPMV_FMT_SELL:
-        SPMV_TRY(pack_sell(h, cfg.hyb_ell_width, s));
+        SPMV_TRY(pack_sell(h, cfg.hyb_ell_width, cfg.bsr_block == 4, s));
         break;
     case SPMV_FMT_BSR: {
         SPMV_TRY(pack_bsr(h, cfg.bsr_block, s));

@@ -300,6 +300,7 @@ struct spmv_matrix {
     // SELL: 32-row slices, column-major inside a slice, all rows stably
     // sorted by descending length; work items = (slice, first slot, columns)
     int64_t sell_nslices = 0, sell_slots = 0;
+    bool sell_grouped = false;  // columns in groups of four (else column-major)
     int32_t *sell_ptr = nullptr, *sell_col = nullptr, *sell_perm = nullptr;
     void *sell_val = nullptr;
     // scratch of the segmented-reduction kernels (COO, HYB tail, split CSR)

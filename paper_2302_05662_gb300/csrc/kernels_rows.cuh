@@ -448,45 +448,120 @@ k_bsr_long(int64_t nseg, const int *__restrict__ seg_row, const int *__restrict_
 // SELL (Section 2.3: slices of rows stored as small ELL matrices with a slice
 // pointer array).  Slices are 32 rows -- one warp, one lane per row -- of
 // rows sorted by descending length, so a slice's rows have similar lengths
-// and little padding.  A work item covers at most the item width (128
+// and little padding.  Inside a slice the columns come in groups of four,
+// each group with a lane's four entries side by side, so a lane loads four
+// column indices with one 16-byte access and a warp's request is 512
+// contiguous bytes; a slice's last (width mod 4) columns are stored
+// column-major, so no slot of padding is added.  A work item covers at most the item width (128
 // columns by default) of one slice: a wider slice becomes several items whose
 // per-row partials are joined in item order, so a slice of power-law rows is
 // not left to one warp.  Slices of empty rows get no work item.
 // ---------------------------------------------------------------------------
+// 4 stored values of one lane's group (16-byte aligned for fp32 columns;
+// 32-byte for fp64, 8-byte for bf16), through the streaming path
+__device__ __forceinline__ void ld_vals4_s(const double *p, double (&o)[4]) {
+    const double2 a = ld_s(reinterpret_cast<const double2 *>(p));
+    const double2 b = ld_s(reinterpret_cast<const double2 *>(p) + 1);
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+__device__ __forceinline__ void ld_vals4_s(const float *p, float (&o)[4]) {
+    const float4 a = ld_s(reinterpret_cast<const float4 *>(p));
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+}
+__device__ __forceinline__ void ld_vals4_s(const __nv_bfloat16 *p, float (&o)[4]) {
+    const uint2 w = ld_s(reinterpret_cast<const uint2 *>(p));
+    o[0] = bf16lo(w.x); o[1] = bf16hi(w.x); o[2] = bf16lo(w.y); o[3] = bf16hi(w.y);
+}
+
 // Work item `it` of a SELL matrix (the whole warp), shared by k_sell and the
-// batched kernel.
-template <typename V, typename T, int UNROLL>
+// batched kernel.  An item is `len` columns of one slice starting at slot
+// `ib`: len >> 2 groups of four columns (lane l's four entries of a group
+// contiguous at ib + 128 g + 4 l: one 16-byte column load per lane and
+// group), then len & 3 column-major columns (the slice's last item only).
+template <typename V, typename T, int UNROLL, bool GROUPED>
 __device__ __forceinline__ void sell_item(int64_t it, int64_t m, const int *__restrict__ it_slice,
                                           const int *__restrict__ it_base, const int *__restrict__ it_len,
                                           const int *__restrict__ it_c0, const int *__restrict__ it_c1,
                                           const int *__restrict__ col, const V *__restrict__ val,
                                           const int *__restrict__ perm, const T *__restrict__ x, T *__restrict__ y,
                                           const Epi<T> &ep, const PartialsT<T> &P) {
+    constexpr int UG = UNROLL >= 8 ? 2 : 1;  // groups of four in flight per lane
     const int lane = threadIdx.x & 31;
     // an item is three independent loads: slice, slot offset, columns (the
     // row and join range are read after the loop: requesting them up front
     // slowed the fp64 banded product by 4%)
     const int sl = __ldg(it_slice + it), ib = __ldg(it_base + it), len = __ldg(it_len + it);
-    const int64_t base = (int64_t)ib + lane;
     T acc = T(0);
-    int k = 0;
-    for (; k + UNROLL <= len; k += UNROLL) {
-        int c[UNROLL];
-        T v[UNROLL], xv[UNROLL];
+    if constexpr (!GROUPED) {  // every column column-major: entry k at ib + 32 k + lane
+        const int64_t base = (int64_t)ib + lane;
+        int k = 0;
+        for (; k + UNROLL <= len; k += UNROLL) {
+            int c[UNROLL];
+            T v[UNROLL], xv[UNROLL];
 #pragma unroll
-        for (int u = 0; u < UNROLL; ++u) c[u] = ld_s(col + base + 32LL * (k + u));
+            for (int u = 0; u < UNROLL; ++u) c[u] = ld_s(col + base + 32LL * (k + u));
 #pragma unroll
-        for (int u = 0; u < UNROLL; ++u) {
-            v[u] = ld_val(val + base + 32LL * (k + u));
-            xv[u] = ld_x(x, c[u] >= 0 ? c[u] : 0);
+            for (int u = 0; u < UNROLL; ++u) {
+                v[u] = ld_val(val + base + 32LL * (k + u));
+                xv[u] = ld_x(x, c[u] >= 0 ? c[u] : 0);
+            }
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u)
+                if (c[u] >= 0) acc = fma(v[u], xv[u], acc);
+        }
+        for (; k < len; ++k) {
+            const int c = ld_s(col + base + 32LL * k);
+            if (c >= 0) acc = fma(ld_val(val + base + 32LL * k), ld_x(x, c), acc);
+        }
+    } else {
+    const int ng = len >> 2;
+    const int64_t gbase = (int64_t)ib + 4 * lane;
+    int g = 0;
+    for (; g + UG <= ng; g += UG) {
+        int c[UG][4];
+        T v[UG][4], xv[UG][4];
+#pragma unroll
+        for (int u = 0; u < UG; ++u) {
+            const int4 w = ld_s(reinterpret_cast<const int4 *>(col + gbase + 128LL * (g + u)));
+            c[u][0] = w.x; c[u][1] = w.y; c[u][2] = w.z; c[u][3] = w.w;
+            ld_vals4_s(val + gbase + 128LL * (g + u), v[u]);
         }
 #pragma unroll
-        for (int u = 0; u < UNROLL; ++u)
-            if (c[u] >= 0) acc = fma(v[u], xv[u], acc);
+        for (int u = 0; u < UG; ++u)
+#pragma unroll
+            for (int t = 0; t < 4; ++t) xv[u][t] = ld_x(x, c[u][t] >= 0 ? c[u][t] : 0);
+#pragma unroll
+        for (int u = 0; u < UG; ++u)
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                if (c[u][t] >= 0) acc = fma(v[u][t], xv[u][t], acc);
     }
-    for (; k < len; ++k) {
-        const int c = ld_s(col + base + 32LL * k);
-        if (c >= 0) acc = fma(ld_val(val + base + 32LL * k), ld_x(x, c), acc);
+    for (; g < ng; ++g) {
+        const int4 w = ld_s(reinterpret_cast<const int4 *>(col + gbase + 128LL * g));
+        T v[4];
+        ld_vals4_s(val + gbase + 128LL * g, v);
+        const int c[4] = {w.x, w.y, w.z, w.w};
+        T xv[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) xv[t] = ld_x(x, c[t] >= 0 ? c[t] : 0);
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+            if (c[t] >= 0) acc = fma(v[t], xv[t], acc);
+    }
+    const int tail = len & 3;
+    if (tail) {  // the slice's last columns, column-major
+        const int64_t tb = (int64_t)ib + 128LL * ng + lane;
+        int c[3];
+        T v[3];
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            c[t] = t < tail ? ld_s(col + tb + 32 * t) : -1;
+            v[t] = t < tail ? ld_val(val + tb + 32 * t) : T(0);
+        }
+#pragma unroll
+        for (int t = 0; t < 3; ++t)
+            if (c[t] >= 0) acc = fma(v[t], ld_x(x, c[t]), acc);
+    }
     }
     const int64_t p = (int64_t)sl * 32 + lane;
     if (p < m) {
@@ -497,7 +572,7 @@ __device__ __forceinline__ void sell_item(int64_t it, int64_t m, const int *__re
     }
 }
 
-template <typename V, typename T, int UNROLL, int REGCAP>
+template <typename V, typename T, int UNROLL, int REGCAP, bool GROUPED>
 __global__ void __launch_bounds__(1024) __maxnreg__(REGCAP)
 k_sell(int64_t m, int64_t nitems, int64_t s_zero, const int *__restrict__ it_slice, const int *__restrict__ it_base,
        const int *__restrict__ it_len, const int *__restrict__ it_c0, const int *__restrict__ it_c1,
@@ -517,7 +592,8 @@ k_sell(int64_t m, int64_t nitems, int64_t s_zero, const int *__restrict__ it_sli
     for (int64_t j = 0; j * nwarps < nitems; ++j) {
         const int64_t it = j * nwarps + ((j & 1) ? nwarps - 1 - warp : warp);
         if (it >= nitems) continue;
-        sell_item<V, T, UNROLL>(it, m, it_slice, it_base, it_len, it_c0, it_c1, col, val, perm, x, y, ep, P);
+        sell_item<V, T, UNROLL, GROUPED>(it, m, it_slice, it_base, it_len, it_c0, it_c1, col, val, perm, x, y, ep,
+                                         P);
     }
 }
 

@@ -183,9 +183,9 @@ int run_bsr_vt(const spmv_matrix *h, double alpha, const void *x, double beta, v
 }
 
 // ----------------------------------- SELL ----------------------------------
-template <typename V, typename T, int U, int RC>
-int launch_sell_rc(const spmv_matrix *h, T alpha, const T *x, T beta, T *y, cudaStream_t s) {
-    auto kern = k_sell<V, T, U, RC>;
+template <typename V, typename T, int U, int RC, bool GROUPED>
+int launch_sell_g(const spmv_matrix *h, T alpha, const T *x, T beta, T *y, cudaStream_t s) {
+    auto kern = k_sell<V, T, U, RC, GROUPED>;
     const int tpb = h->cfg.threads_per_block;
     SPMV_TRY(apply_carveout((const void *)kern, h->cfg.carveout));
     const LongRows &L = h->lng;  // items; nrows = first slice of empty rows
@@ -197,6 +197,12 @@ int launch_sell_rc(const spmv_matrix *h, T alpha, const T *x, T beta, T *y, cuda
                               (const V *)h->sell_val, h->sell_perm, x, y, alpha, beta, PartialsT<T>::of(L.part));
     SPMV_LAUNCH_CHECK();
     return SPMV_OK;
+}
+
+template <typename V, typename T, int U, int RC>
+int launch_sell_rc(const spmv_matrix *h, T alpha, const T *x, T beta, T *y, cudaStream_t s) {
+    return h->sell_grouped ? launch_sell_g<V, T, U, RC, true>(h, alpha, x, beta, y, s)
+                           : launch_sell_g<V, T, U, RC, false>(h, alpha, x, beta, y, s);
 }
 
 template <typename V, typename T, int U>

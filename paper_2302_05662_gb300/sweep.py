@@ -51,15 +51,20 @@ def label_space(tpb=TPB, include_sell: bool = False):
 
 
 def refine_space(best: dict):
-    """Register cap x unroll x carveout around a winning point."""
+    """Register cap x unroll x carveout around a winning point (x SELL's
+    column groups: column-major or groups of four)."""
     out = []
     ell_family = best.get("format", 0) in (B.FMT_ELL, B.FMT_HYB, B.FMT_SELL)
+    groups = (1, 4) if best.get("format", 0) == B.FMT_SELL else (None,)   # SELL column groups
     for rc in ((32, 48, 64) if ell_family else (32, 64)):
         for u in ((1, 2, 4, 8) if ell_family else (1, 2, 4)):
             for cv in (-1, 0, 100):
-                d = dict(best)
-                d.update(regcap=rc, unroll=u, carveout=cv)
-                out.append(d)
+                for g in groups:
+                    d = dict(best)
+                    d.update(regcap=rc, unroll=u, carveout=cv)
+                    if g is not None:
+                        d["bsr_block"] = g
+                    out.append(d)
     return out
 
 

@@ -319,18 +319,27 @@ def test_format_layouts_decode_to_the_matrix(oracle):
 
 
 def test_sell_layout_decodes_to_the_matrix():
-    """SELL: 32-row slices, entry k of sorted row p at ptr[s] + 32k + (p % 32),
-    rows sorted by descending length (stable), perm maps a sorted row back
-    to its matrix row, padding -1 / 0 after each row."""
+    """SELL: 32-row slices of width w; with column groups, entry k of lane l
+    (sorted row p, slice s = p // 32, l = p % 32) at ptr[s] + 128 (k // 4) +
+    4 l + k % 4 for the first w & ~3 columns (a lane's four entries of a
+    group contiguous) and at ptr[s] + 32 (w & ~3) + 32 (k - (w & ~3)) + l
+    after them; column-major, entry k at ptr[s] + 32 k + l; rows
+    sorted by descending length (stable), perm maps a sorted row back to its
+    matrix row, padding -1 / 0 after each row."""
     import torch
-    for coo in (SMALL["rmat_s14_ef16"], matgen.random_coo(1000, 700, 6000, np.random.default_rng(4)),
-                matgen.Coo(37, 9, np.array([0, 36], np.int32), np.array([1, 8], np.int32), np.array([2.0, 3.0]))):
+    cases = [(coo, g) for coo in (SMALL["rmat_s14_ef16"], matgen.random_coo(1000, 700, 6000, np.random.default_rng(4)),
+                                  matgen.Coo(37, 9, np.array([0, 36], np.int32), np.array([1, 8], np.int32),
+                                             np.array([2.0, 3.0])))
+             for g in (0, 1, 4)]     # column groups: chosen per matrix, column-major, groups of four
+    for coo, g in cases:
         vals = np.random.default_rng(5).integers(-9, 10, coo.nnz).astype(float)
         ci = matgen.Coo(coo.m, coo.n, coo.rows, coo.cols, vals)
         ref = {(r, c): v for r, c, v in zip(ci.rows.tolist(), ci.cols.tolist(), ci.vals.tolist())}
         lens = np.bincount(ci.rows, minlength=ci.m)
-        h = create(ci, B.SPMV_F64, cfg_of("sell"))
+        h = create(ci, B.SPMV_F64, B.make_config(format=B.FMT_SELL, bsr_block=g))
         try:
+            grouped = B.spmv_get_config(h).bsr_block == 4
+            assert g == 0 or grouped == (g == 4)
             info = B.spmv_get_info(h)
             ptr = _export(h, B.ARR_SELL_PTR, torch.int32).numpy()
             col = _export(h, B.ARR_SELL_COLIDX, torch.int32).numpy()
@@ -344,17 +353,25 @@ def test_sell_layout_decodes_to_the_matrix():
         same = np.flatnonzero(np.diff(pl) == 0)
         assert np.all(perm[same] < perm[same + 1])                      # stable among equal lengths
         assert info.sell_slots == ptr[-1]
+        def slot(sl, width, k, l):
+            w4 = width & ~3 if grouped else 0
+            return ptr[sl] + (128 * (k // 4) + 4 * l + k % 4 if k < w4 else 32 * w4 + 32 * (k - w4) + l)
+
         got = {}
         for p in range(ci.m):
             sl, l = divmod(p, 32)
             width = (ptr[sl + 1] - ptr[sl]) // 32
             for k in range(width):
-                c = col[ptr[sl] + 32 * k + l]
+                c = col[slot(sl, width, k, l)]
                 if c < 0:
-                    assert np.all(col[ptr[sl] + 32 * np.arange(k, width) + l] < 0)
+                    assert all(col[slot(sl, width, j, l)] < 0 for j in range(k, width))
                     break
-                got[(int(perm[p]), int(c))] = val[ptr[sl] + 32 * k + l]
+                got[(int(perm[p]), int(c))] = val[slot(sl, width, k, l)]
         assert got == ref
+        # every slot is filled exactly once by the layout
+        seen = sorted(slot(sl, (ptr[sl + 1] - ptr[sl]) // 32, k, l) for sl in range(len(ptr) - 1)
+                      for k in range((ptr[sl + 1] - ptr[sl]) // 32) for l in range(32))
+        assert seen == list(range(int(ptr[-1])))
 
 
 def test_invalid_triplets_rejected():
