@@ -318,11 +318,10 @@ NAMES = ("stencil27_128^3", "poisson16_2^20", "rmat_s20_ef16", "banded_2^20_w32"
 # value type); summaries and commands in profiles/.  A kernel missing here
 # reports traffic null.
 NCU_TRAFFIC = {
-    ("bsr", "banded_2^20_w32", "f64"): (602.3e6, "profiles/bsr_banded_2p20_w32_f64.md"),
-    ("ell", "stencil27_128^3", "f64"): (694.8e6, "profiles/ell_stencil27_128_f64.md"),
     ("sell", "banded_2^20_w32", "f64"): (835.5e6, "profiles/sell_banded_2p20_w32_f64.md"),
-    ("sell", "rmat_s20_ef16", "f64"): (217.6e6, "profiles/traffic_f64_formats.md"),
-    ("sell", "poisson16_2^20", "f64"): (216.2e6, "profiles/traffic_f64_formats.md"),
+    ("sell", "rmat_s20_ef16", "f64"): (225.4e6, "profiles/sell_rmat_s20_f64.md"),
+    ("csr", "stencil27_128^3", "f64"): (712.0e6, "profiles/csr_vector_stencil27_128_f64.md"),
+    ("csr_split", "stencil27_128^3", "f64"): (712.4e6, "profiles/csr_tiles_stencil27_128_f64.md"),
 }
 FMT_KEYS = {0: "csr", 1: "ell", 2: "coo", 3: "hyb", 4: "bsr", 5: "sell"}
 
