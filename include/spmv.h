@@ -91,10 +91,15 @@ typedef enum {
                       /* descending length (Sec. 2.3 SELL)                 */
 } spmv_format;
 
-/* threads_per_row value that selects the nnz-balanced CSR kernel: tiles of
- * a fixed number of nonzeros, each bulk-copied into shared memory while the
- * thread block multiplies the previous one, rows summed by groups of lanes
- * (1..8 from the mean row length) and joined across tiles. */
+/* threads_per_row value that selects the nnz-balanced CSR kernels (Sec. 2.3:
+ * CSR's load imbalance on uneven rows).  Two forms, chosen by hyb_ell_width:
+ * warp chunks (0, the default): chunks of 4 x unroll x 32 nonzeros, one warp
+ * each, a lane summing 4 x unroll consecutive entries, the rows recovered
+ * from the row pointers (no row index per entry) and joined across lanes and
+ * chunks; or staged tiles (hyb_ell_width nonzeros per tile): each tile
+ * bulk-copied into shared memory while the thread block multiplies the
+ * previous one, rows summed by groups of lanes (1..8 from the mean row
+ * length) and joined across tiles. */
 #define SPMV_TPR_SPLIT (-1)
 
 /*
@@ -126,15 +131,19 @@ typedef enum {
  *                     columns side by side: 16-byte loads) or 1 (column-
  *                     major); 0 = 4 unless the longest row exceeds 32 mean
  *                     rows plus 32 (power-law rows: mostly narrow slices,
- *                     where column-major runs faster), then 1.
+ *                     where column-major runs faster), then 1.  CSR with 1
+ *                     or 2 lanes per row: entries per lane load, 8 (32-byte
+ *                     loads) or 4 (16-byte loads); 0 = 8 when a lane's part
+ *                     of a mean-length row holds 16 or more entries, else 4
+ *                     (wider groups mask more slots at a part's ends).
  *   hyb_ell_width     HYB ELL width; 0 applies the width rule (the largest
  *                     k such that at least max(4096, m/3) rows hold k or
  *                     more nonzeros).  SELL: columns of a slice per work
  *                     item, a multiple of 4 in 8..65536 (0 = 128); wider
  *                     slices are split into several items joined in order.  CSR with
- *                     SPMV_TPR_SPLIT: nonzeros per tile staged through
- *                     shared memory, a multiple of 256 in [256, 8192]
- *                     (0 = 4096).
+ *                     SPMV_TPR_SPLIT: 0 = warp chunks, else nonzeros per
+ *                     tile staged through shared memory, a multiple of 256
+ *                     in [256, 8192].
  * spmv_config_default() fills the defaults (carveout = -1; unroll and
  * regcap 0, resolved per format and value type when the configuration is
  * applied; spmv_get_config returns the resolved values).

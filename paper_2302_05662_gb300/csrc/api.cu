@@ -155,6 +155,11 @@ int resolve_config(const spmv_matrix *h, const spmv_config *in, spmv_config *out
         // columns wide and column-major runs faster); BSR: 4 x 4 blocks
         const double mean = h->m > 0 ? (double)h->nnz / (double)h->m : 0.0;
         c.bsr_block = c.format == SPMV_FMT_SELL && (double)h->max_row > 32.0 * mean + 32.0 ? 1 : 4;
+        // CSR vector with one or two lanes per row: 8-entry groups (32-byte
+        // loads) once a lane's part of a mean row holds 16 or more entries,
+        // else 4 (fewer masked slots: shorter rows); set below with the
+        // lanes per row
+        if (c.format == SPMV_FMT_CSR) c.bsr_block = 0;
     }
     if (c.format < SPMV_FMT_CSR || c.format > SPMV_FMT_SELL) {
         set_error("config: unknown format %d", c.format);
@@ -177,8 +182,11 @@ int resolve_config(const spmv_matrix *h, const spmv_config *in, spmv_config *out
         set_error("config: carveout %d not in [-1, 100]", c.carveout);
         return SPMV_ERR_INVALID;
     }
-    if (c.format == SPMV_FMT_SELL ? (c.bsr_block != 1 && c.bsr_block != 4) : (c.bsr_block != 2 && c.bsr_block != 4)) {
-        set_error("config: bsr_block %d not in {2, 4} ({1, 4} for SELL column groups)", c.bsr_block);
+    if (c.format == SPMV_FMT_SELL   ? (c.bsr_block != 1 && c.bsr_block != 4)
+        : c.format == SPMV_FMT_CSR  ? (c.bsr_block != 0 && c.bsr_block != 4 && c.bsr_block != 8)
+                                    : (c.bsr_block != 2 && c.bsr_block != 4)) {
+        set_error("config: bsr_block %d not in {2, 4} ({1, 4} for SELL column groups, {4, 8} for CSR load groups)",
+                  c.bsr_block);
         return SPMV_ERR_INVALID;
     }
     if (c.hyb_ell_width < 0) {
@@ -197,14 +205,18 @@ int resolve_config(const spmv_matrix *h, const spmv_config *in, spmv_config *out
     switch (c.format) {
     case SPMV_FMT_CSR:
         if (c.threads_per_row == 0) c.threads_per_row = default_tpr(h);
+        if (c.bsr_block == 0) {
+            const double mean = h->m > 0 ? (double)h->nnz / (double)h->m : 0.0;
+            c.bsr_block = c.threads_per_row >= 1 && mean / c.threads_per_row >= 16.0 ? 8 : 4;
+        }
         if (c.threads_per_row != SPMV_TPR_SPLIT && !pow2_in(c.threads_per_row, 1, 32)) {
             set_error("config: CSR threads_per_row %d not in {1..32 powers of two, -1}", c.threads_per_row);
             return SPMV_ERR_INVALID;
         }
-        if (c.threads_per_row == SPMV_TPR_SPLIT) {  // nonzeros per staged tile
-            if (c.hyb_ell_width == 0) c.hyb_ell_width = 4096;
-            if (c.hyb_ell_width < 256 || c.hyb_ell_width > 8192 || c.hyb_ell_width % 256 != 0) {
-                set_error("config: CSR tile size %d not a multiple of 256 in [256, 8192]", c.hyb_ell_width);
+        if (c.threads_per_row == SPMV_TPR_SPLIT) {  // 0: warp chunks; else nonzeros per staged tile
+            if (c.hyb_ell_width != 0 &&
+                (c.hyb_ell_width < 256 || c.hyb_ell_width > 8192 || c.hyb_ell_width % 256 != 0)) {
+                set_error("config: CSR tile size %d not 0 or a multiple of 256 in [256, 8192]", c.hyb_ell_width);
                 return SPMV_ERR_INVALID;
             }
         }
@@ -357,7 +369,8 @@ void spmv_config_default(spmv_config *cfg, int32_t format) {
     cfg->unroll = 0;  // per format and value type, resolved when applied
     cfg->regcap = 0;
     cfg->carveout = -1;
-    cfg->bsr_block = format == SPMV_FMT_SELL ? 0 : 4;  // SELL: column groups chosen per matrix
+    // SELL column groups and CSR load groups chosen per matrix
+    cfg->bsr_block = format == SPMV_FMT_SELL || format == SPMV_FMT_CSR ? 0 : 4;
     cfg->hyb_ell_width = 0;
 }
 

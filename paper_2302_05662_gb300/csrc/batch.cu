@@ -49,7 +49,7 @@ struct BatchMat {
     double alpha, beta;
     int64_t m, nnz;
     int64_t part_off;  // first chunk of this matrix in the batch partials
-    const int *meta0;  // split: row of each chunk's first entry
+    const int *meta0;  // split: first row starting at or after each chunk's first entry
     int mode;          // CSR: 0 split, else lanes per row
     int fmt;           // the handle's format: SPMV_FMT_ELL, SPMV_FMT_SELL, or CSR (any other)
     // ELL: column-major arrays, int32 columns or 16-bit offsets
@@ -108,10 +108,12 @@ void describe_format(const spmv_matrix *h, BatchMat &M) {
     }
 }
 
+// register budget: 16 items per lane, or fp64 sums, need more than 64
 template <typename V, typename T, int ITEMS>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(512) __maxnreg__(ITEMS >= 16 ? 128 : (sizeof(T) == 8 ? 96 : 64))
 k_batch(const BatchMat *__restrict__ mats, int count, const int64_t *__restrict__ item_off, int64_t total,
         unsigned long long *counter, const PartialsT<T> P) {
+    __shared__ MergeSmem<ITEMS> s_merge[16];  // split chunks: one per warp
     const int lane = threadIdx.x & 31;
     for (;;) {
         unsigned long long item = 0;
@@ -156,7 +158,9 @@ k_batch(const BatchMat *__restrict__ mats, int count, const int64_t *__restrict_
             Pm.tail += M.part_off;
             Pm.count += M.part_off;
             Pm.xslot += M.part_off;
-            csr_split_chunk<V, T, ITEMS>(local, M.nnz, M.m, M.rowptr, M.colidx, vals, x, y, ep, M.meta0, Pm);
+            csr_merge_chunk<V, T, ITEMS>(local, M.nnz, M.m, M.rowptr, M.colidx, vals, x, y, ep, __ldg(M.meta0 + local),
+                                         __ldg(M.meta0 + local + 1), Pm,
+                                         s_merge[threadIdx.x >> 5]);
         } else {
             const int64_t base = local * 32;
             const int big = 0x7fffffff;
@@ -261,7 +265,7 @@ int build(spmv_batch *b, cudaStream_t s) {
         if (M.fmt == SPMV_FMT_CSR && M.mode == 0) {
             const int64_t nch = (h->nnz + C - 1) / C;
             SPMV_CUDA_TRY(dev_malloc((void **)&b->metas[i], sizeof(int32_t) * (nch + 1)));
-            SPMV_TRY(build_split_meta(h->rowptr, h->m, h->nnz, C, b->metas[i], s));
+            SPMV_TRY(build_merge_meta(h->rowptr, h->m, h->nnz, C, b->metas[i], s));
             M.meta0 = b->metas[i];
             M.part_off = chunks_total;
             chunks_total += nch;
@@ -455,7 +459,7 @@ int spmv_batch_tune(spmv_batch_handle b, void *stream) {
             int st = SPMV_OK;
             if (mode == 0) {
                 if (dev_malloc((void **)&meta, sizeof(int32_t) * (off[1] + 1)) != cudaSuccess) st = SPMV_ERR_OOM;
-                if (st == SPMV_OK) st = build_split_meta(h->rowptr, h->m, h->nnz, C, meta, s);
+                if (st == SPMV_OK) st = build_merge_meta(h->rowptr, h->m, h->nnz, C, meta, s);
                 M.meta0 = meta;
                 if (st == SPMV_OK) st = alloc_partials(&one.part, off[1], 1, one.vt, s);
             }

@@ -522,6 +522,22 @@ __global__ void k_seg_meta_split(const int *rowptr, int64_t m, int64_t nnz, int 
     }
 }
 
+// split CSR by warp chunks: first row starting at or after each chunk's
+// first entry (lower bound of c*C in rowptr[0..m)); entry nchunks = m
+__global__ void k_seg_meta_merge(const int *rowptr, int64_t m, int C, int64_t nchunks, int *meta) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c <= nchunks; c += stride) {
+        if (c == nchunks) { meta[c] = (int)m; continue; }
+        const int64_t k = c * (int64_t)C;
+        int64_t lo = 0, hi = m;  // first r in [0, m] with r == m or rowptr[r] >= k
+        while (lo < hi) {
+            const int64_t mid = lo + ((hi - lo) >> 1);
+            if (rowptr[mid] >= k) hi = mid; else lo = mid + 1;
+        }
+        meta[c] = (int)lo;
+    }
+}
+
 __global__ void k_fill_u64(unsigned long long *p, int64_t n, unsigned long long v) {
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) p[i] = v;
@@ -1308,17 +1324,16 @@ int pack_sell(spmv_matrix *h, int kmax, bool grouped, cudaStream_t s) {
 }
 }  // namespace
 
-int build_split_meta(const int32_t *rowptr, int64_t m, int64_t nnz, int C, int32_t *meta0, cudaStream_t s) {
+int build_merge_meta(const int32_t *rowptr, int64_t m, int64_t nnz, int C, int32_t *meta, cudaStream_t s) {
     const int64_t nchunks = (nnz + C - 1) / C;
-    if (m == 0) return SPMV_OK;
-    k_seg_meta_split<<<grid1d(nchunks + 1, 256), 256, 0, s>>>(rowptr, m, nnz, C, nchunks, meta0);
+    k_seg_meta_merge<<<grid1d(nchunks + 1, 256), 256, 0, s>>>(rowptr, m, C, nchunks, meta);
     SPMV_CUDA_TRY(cudaGetLastError());
     return SPMV_OK;
 }
 
-int ensure_seg_scratch(spmv_matrix *h, int items, bool split_csr, cudaStream_t s) {
+int ensure_seg_scratch(spmv_matrix *h, int items, int kind, cudaStream_t s) {
     SegScratch &g = h->seg;
-    const int64_t nnz = split_csr ? h->nnz : (h->cfg.format == SPMV_FMT_HYB ? h->hyb_nnz : h->nnz);
+    const int64_t nnz = kind != SEG_COO ? h->nnz : (h->cfg.format == SPMV_FMT_HYB ? h->hyb_nnz : h->nnz);
     const int C = 32 * items;
     const int64_t nchunks = (nnz + C - 1) / C;
     auto f = [](void *p) { if (p) cudaFree(p); };
@@ -1332,8 +1347,10 @@ int ensure_seg_scratch(spmv_matrix *h, int items, bool split_csr, cudaStream_t s
     SPMV_TRY(alloc_partials(&g.part, nchunks, 1, h->vt, s));
     if (nchunks > 0) {
         unsigned grid = grid1d(nchunks + 1, 256);
-        if (split_csr) {
+        if (kind == SEG_TILES) {
             k_seg_meta_split<<<grid, 256, 0, s>>>(h->rowptr, h->m, nnz, C, nchunks, g.meta0);
+        } else if (kind == SEG_MERGE) {
+            k_seg_meta_merge<<<grid, 256, 0, s>>>(h->rowptr, h->m, C, nchunks, g.meta0);
         } else if (h->cfg.format == SPMV_FMT_HYB) {
             k_seg_meta_coo<<<grid, 256, 0, s>>>(h->hyb_rows, h->hyb_ptr, nnz, C, nchunks, g.meta0, g.meta1);
         } else {
@@ -1365,8 +1382,10 @@ int pack_format(spmv_matrix *h, const spmv_config &cfg, cudaStream_t s) {
     switch (cfg.format) {
     case SPMV_FMT_CSR:
         if (cfg.threads_per_row == SPMV_TPR_SPLIT) {
-            // nonzero tiles: hyb_ell_width = nonzeros per tile (a multiple of 256)
-            SPMV_TRY(ensure_seg_scratch(h, cfg.hyb_ell_width / 32, true, s));
+            // hyb_ell_width 0: warp chunks of 32 * items entries; else staged
+            // tiles of hyb_ell_width nonzeros (a multiple of 256)
+            if (cfg.hyb_ell_width == 0) SPMV_TRY(ensure_seg_scratch(h, items, SEG_MERGE, s));
+            else SPMV_TRY(ensure_seg_scratch(h, cfg.hyb_ell_width / 32, SEG_TILES, s));
         } else {
             // rows needing more than 32 steps of their lane group go to whole blocks
             const int64_t thr = std::max<int64_t>(512, 32LL * cfg.threads_per_row * cfg.unroll);
@@ -1387,7 +1406,7 @@ int pack_format(spmv_matrix *h, const spmv_config &cfg, cudaStream_t s) {
     case SPMV_FMT_COO:
         SPMV_TRY(dalloc(&h->coo_rows, (size_t)h->nnz));
         SPMV_TRY(expand_rows(h->rowptr, h->m, h->nnz, h->coo_rows, s));
-        SPMV_TRY(ensure_seg_scratch(h, items, false, s));
+        SPMV_TRY(ensure_seg_scratch(h, items, SEG_COO, s));
         break;
     case SPMV_FMT_HYB: {
         int64_t width = cfg.hyb_ell_width;
@@ -1395,7 +1414,7 @@ int pack_format(spmv_matrix *h, const spmv_config &cfg, cudaStream_t s) {
         width = std::min<int64_t>(width, h->max_row);
         SPMV_TRY(pack_hyb(h, width, s));
         h->cfg.hyb_ell_width = (int32_t)width;
-        SPMV_TRY(ensure_seg_scratch(h, items, false, s));
+        SPMV_TRY(ensure_seg_scratch(h, items, SEG_COO, s));
         break;
     }
     case SPMV_FMT_SELL:

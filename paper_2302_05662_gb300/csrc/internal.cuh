@@ -148,30 +148,58 @@ __device__ __forceinline__ float ld_val_c(const __nv_bfloat16 *p) {
     return __uint_as_float((uint32_t)__ldg(reinterpret_cast<const unsigned short *>(p)) << 16);
 }
 
-// N contiguous stored values starting at an N-aligned element (vector loads)
-template <int N>
+// N consecutive entries from a 16-byte aligned address with 16-byte loads,
+// or, with WIDE, from a 32-byte aligned address with 32-byte loads (the
+// 256-bit global loads of sm_100 and later: half the load instructions and
+// L1 wavefronts for the same bytes).
+__device__ __forceinline__ void ld_s8(const int *p, int *o) {
+    asm("ld.global.nc.L1::no_allocate.v8.s32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=r"(o[0]), "=r"(o[1]), "=r"(o[2]), "=r"(o[3]), "=r"(o[4]), "=r"(o[5]), "=r"(o[6]), "=r"(o[7])
+        : "l"(p));
+}
+__device__ __forceinline__ void ld_s4(const double *p, double *o) {
+    asm("ld.global.nc.L1::no_allocate.v4.f64 {%0,%1,%2,%3}, [%4];"
+        : "=d"(o[0]), "=d"(o[1]), "=d"(o[2]), "=d"(o[3]) : "l"(p));
+}
+__device__ __forceinline__ void ld_s8(const float *p, float *o) {
+    asm("ld.global.nc.L1::no_allocate.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(o[0]), "=f"(o[1]), "=f"(o[2]), "=f"(o[3]), "=f"(o[4]), "=f"(o[5]), "=f"(o[6]), "=f"(o[7])
+        : "l"(p));
+}
+
+template <int N, bool WIDE = false>
 __device__ __forceinline__ void ld_vals_vec(const double *p, double (&o)[N]) {
     static_assert(N % 2 == 0, "");
+    if constexpr (WIDE && N % 4 == 0) {
 #pragma unroll
-    for (int i = 0; i < N / 2; ++i) {
-        double2 d = ld_s(reinterpret_cast<const double2 *>(p) + i);
-        o[2 * i] = d.x;
-        o[2 * i + 1] = d.y;
+        for (int i = 0; i < N / 4; ++i) ld_s4(p + 4 * i, o + 4 * i);
+    } else {
+#pragma unroll
+        for (int i = 0; i < N / 2; ++i) {
+            double2 d = ld_s(reinterpret_cast<const double2 *>(p) + i);
+            o[2 * i] = d.x;
+            o[2 * i + 1] = d.y;
+        }
     }
 }
-template <int N>
+template <int N, bool WIDE = false>
 __device__ __forceinline__ void ld_vals_vec(const float *p, float (&o)[N]) {
     static_assert(N % 4 == 0, "");
+    if constexpr (WIDE && N % 8 == 0) {
 #pragma unroll
-    for (int i = 0; i < N / 4; ++i) {
-        float4 d = ld_s(reinterpret_cast<const float4 *>(p) + i);
-        o[4 * i] = d.x; o[4 * i + 1] = d.y; o[4 * i + 2] = d.z; o[4 * i + 3] = d.w;
+        for (int i = 0; i < N / 8; ++i) ld_s8(p + 8 * i, o + 8 * i);
+    } else {
+#pragma unroll
+        for (int i = 0; i < N / 4; ++i) {
+            float4 d = ld_s(reinterpret_cast<const float4 *>(p) + i);
+            o[4 * i] = d.x; o[4 * i + 1] = d.y; o[4 * i + 2] = d.z; o[4 * i + 3] = d.w;
+        }
     }
 }
-template <int N>
+template <int N, bool WIDE = false>
 __device__ __forceinline__ void ld_vals_vec(const __nv_bfloat16 *p, float (&o)[N]) {
     static_assert(N % 4 == 0, "");
-    if constexpr (N % 8 == 0) {
+    if constexpr (N % 8 == 0) {  // 8 bf16 values are one 16-byte load
 #pragma unroll
         for (int i = 0; i < N / 8; ++i) {
             uint4 w = ld_s(reinterpret_cast<const uint4 *>(p) + i);
@@ -189,13 +217,18 @@ __device__ __forceinline__ void ld_vals_vec(const __nv_bfloat16 *p, float (&o)[N
         }
     }
 }
-template <int N>
+template <int N, bool WIDE = false>
 __device__ __forceinline__ void ld_idx_vec(const int *p, int (&o)[N]) {
     static_assert(N % 4 == 0, "");
+    if constexpr (WIDE && N % 8 == 0) {
 #pragma unroll
-    for (int i = 0; i < N / 4; ++i) {
-        int4 d = ld_s(reinterpret_cast<const int4 *>(p) + i);
-        o[4 * i] = d.x; o[4 * i + 1] = d.y; o[4 * i + 2] = d.z; o[4 * i + 3] = d.w;
+        for (int i = 0; i < N / 8; ++i) ld_s8(p + 8 * i, o + 8 * i);
+    } else {
+#pragma unroll
+        for (int i = 0; i < N / 4; ++i) {
+            int4 d = ld_s(reinterpret_cast<const int4 *>(p) + i);
+            o[4 * i] = d.x; o[4 * i + 1] = d.y; o[4 * i + 2] = d.z; o[4 * i + 3] = d.w;
+        }
     }
 }
 
@@ -249,7 +282,8 @@ struct SegScratch {
     int items = 0;            // items per lane (chunk = 32 * items entries)
     int64_t nchunks = 0;
     int32_t *meta0 = nullptr; // COO: first chunk of the chunk's head row;
-                              // split CSR: row of the chunk's first entry
+                              // staged tiles: row of the tile's first entry;
+                              // warp chunks: first row starting at or after it
     int32_t *meta1 = nullptr; // COO: last chunk of the chunk's tail row
     Partials part;
 };
@@ -330,8 +364,10 @@ void free_packed(spmv_matrix *h);
 int expand_rows(const int32_t *rowptr, int64_t m, int64_t nnz, int32_t *rows_out,
                 cudaStream_t s);
 int decode_ell_columns(const spmv_matrix *h, int32_t *d_out, cudaStream_t s);
-int ensure_seg_scratch(spmv_matrix *h, int items, bool split_csr, cudaStream_t s);
-int build_split_meta(const int32_t *rowptr, int64_t m, int64_t nnz, int C, int32_t *meta0, cudaStream_t s);
+// chunk metadata kinds: COO / HYB tail, staged CSR tiles, CSR warp chunks
+enum { SEG_COO = 0, SEG_TILES = 1, SEG_MERGE = 2 };
+int ensure_seg_scratch(spmv_matrix *h, int items, int kind, cudaStream_t s);
+int build_merge_meta(const int32_t *rowptr, int64_t m, int64_t nnz, int C, int32_t *meta, cudaStream_t s);
 int alloc_partials(Partials *p, int64_t units, int stride, int vt, cudaStream_t s);
 void free_partials(Partials *p);
 int build_long_rows(spmv_matrix *h, const int32_t *rowptr, int64_t nrows, int64_t threshold, int64_t seg,

@@ -38,37 +38,69 @@ __device__ __forceinline__ void ld_vals4_c(const __nv_bfloat16 *p, float (&o)[4]
     o[0] = bf16lo(w.x); o[1] = bf16hi(w.x); o[2] = bf16lo(w.y); o[3] = bf16hi(w.y);
 }
 
-// Entries [a, b) of one row summed by one lane with 16-byte loads: the lane
-// walks the aligned groups of 4 entries covering its range (the first and
-// last group masked), G groups in flight.  The column and value arrays are
-// padded past nnz, so the last group's load stays inside them.
-template <typename V, typename T, int G>
+// 8 stored entries starting at a multiple of 8: 32-byte loads (the 256-bit
+// global loads of sm_100 and later), L1-allocating as above
+__device__ __forceinline__ void ld_idx8_c(const int *p, int (&o)[8]) {
+    asm("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(o[0]), "=r"(o[1]), "=r"(o[2]), "=r"(o[3]), "=r"(o[4]), "=r"(o[5]), "=r"(o[6]), "=r"(o[7])
+        : "l"(p));
+}
+__device__ __forceinline__ void ld_vals8_c(const double *p, double (&o)[8]) {
+    asm("ld.global.nc.v4.f64 {%0, %1, %2, %3}, [%4];" : "=d"(o[0]), "=d"(o[1]), "=d"(o[2]), "=d"(o[3]) : "l"(p));
+    asm("ld.global.nc.v4.f64 {%0, %1, %2, %3}, [%4];" : "=d"(o[4]), "=d"(o[5]), "=d"(o[6]), "=d"(o[7]) : "l"(p + 4));
+}
+__device__ __forceinline__ void ld_vals8_c(const float *p, float (&o)[8]) {
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(o[0]), "=f"(o[1]), "=f"(o[2]), "=f"(o[3]), "=f"(o[4]), "=f"(o[5]), "=f"(o[6]), "=f"(o[7])
+        : "l"(p));
+}
+__device__ __forceinline__ void ld_vals8_c(const __nv_bfloat16 *p, float (&o)[8]) {
+    const uint4 w = __ldg(reinterpret_cast<const uint4 *>(p));
+    o[0] = bf16lo(w.x); o[1] = bf16hi(w.x); o[2] = bf16lo(w.y); o[3] = bf16hi(w.y);
+    o[4] = bf16lo(w.z); o[5] = bf16hi(w.z); o[6] = bf16lo(w.w); o[7] = bf16hi(w.w);
+}
+
+// one aligned group of GW entries: columns and values
+template <int GW, typename V, typename T>
+__device__ __forceinline__ void ld_group_c(const int *cp, const V *vp, int (&c)[GW], T (&v)[GW]) {
+    if constexpr (GW == 8) {
+        ld_idx8_c(cp, c);
+        ld_vals8_c(vp, v);
+    } else {
+        const int4 w = __ldg(reinterpret_cast<const int4 *>(cp));
+        c[0] = w.x; c[1] = w.y; c[2] = w.z; c[3] = w.w;
+        ld_vals4_c(vp, v);
+    }
+}
+
+// Entries [a, b) of one row summed by one lane with wide loads: the lane
+// walks the aligned groups of GW entries (4: 16-byte loads; 8: 32-byte
+// loads) covering its range, the first and last group masked, G groups in
+// flight.  The column and value arrays are padded to a multiple of 8
+// entries past nnz, so the last group's load stays inside them.
+template <typename V, typename T, int G, int GW>
 __device__ __forceinline__ T csr_lane_range(int a, int b, const int *__restrict__ colidx, const V *__restrict__ vals,
                                             const T *__restrict__ x) {
     T acc = T(0);
-    for (int q = a & ~3; q < b; q += 4 * G) {
-        int c[G][4];
-        T v[G][4], xv[G][4];
+    for (int q = a & ~(GW - 1); q < b; q += GW * G) {
+        int c[G][GW];
+        T v[G][GW], xv[G][GW];
 #pragma unroll
         for (int g = 0; g < G; ++g) {
-            const int gq = q + 4 * g;
-            if (gq < b) {
-                const int4 w = __ldg(reinterpret_cast<const int4 *>(colidx + gq));
-                c[g][0] = w.x; c[g][1] = w.y; c[g][2] = w.z; c[g][3] = w.w;
-                ld_vals4_c(vals + gq, v[g]);
-            }
+            const int gq = q + GW * g;
+            if (gq < b) ld_group_c<GW>(colidx + gq, vals + gq, c[g], v[g]);
 #pragma unroll
-            for (int t = 0; t < 4; ++t)
+            for (int t = 0; t < GW; ++t)
                 if (gq >= b || gq + t < a || gq + t >= b) c[g][t] = -1;
         }
 #pragma unroll
         for (int g = 0; g < G; ++g)
 #pragma unroll
-            for (int t = 0; t < 4; ++t) xv[g][t] = c[g][t] >= 0 ? ld_x(x, c[g][t]) : T(0);
+            for (int t = 0; t < GW; ++t) xv[g][t] = c[g][t] >= 0 ? ld_x(x, c[g][t]) : T(0);
 #pragma unroll
         for (int g = 0; g < G; ++g)
 #pragma unroll
-            for (int t = 0; t < 4; ++t)
+            for (int t = 0; t < GW; ++t)
                 if (c[g][t] >= 0) acc = fma(v[g][t], xv[g][t], acc);
     }
     return acc;
@@ -76,9 +108,9 @@ __device__ __forceinline__ T csr_lane_range(int a, int b, const int *__restrict_
 
 // Rows [base, base + 32) with TPR lanes per row; the whole warp calls it.
 // With one or two lanes per row each lane sums a contiguous part of its row
-// with 16-byte loads (csr_lane_range); with more lanes, the lanes of a row
+// with 16- or 32-byte loads (csr_lane_range); with more lanes, the lanes of a row
 // take interleaved entries, so a warp's loads of a row are contiguous.
-template <typename V, typename T, int TPR, int UNROLL>
+template <typename V, typename T, int TPR, int UNROLL, int GW = 4>
 __device__ __forceinline__ void csr_vector_rows(int64_t base, int64_t m, const int *__restrict__ rowptr,
                                                 const int *__restrict__ colidx, const V *__restrict__ vals,
                                                 const T *__restrict__ x, T *__restrict__ y, const Epi<T> &ep,
@@ -99,11 +131,11 @@ __device__ __forceinline__ void csr_vector_rows(int64_t base, int64_t m, const i
         T acc = T(0);
         if constexpr (TPR <= 2) {
             if (!skip) {
-                // lane sub takes [s, mid) or [mid, e), mid on a 4-entry boundary
-                int mid = TPR == 1 ? e : ((s + (e - s) / 2 + 3) & ~3);
+                // lane sub takes [s, mid) or [mid, e), mid on a group boundary
+                int mid = TPR == 1 ? e : ((s + (e - s) / 2 + GW - 1) & ~(GW - 1));
                 mid = mid < s ? s : (mid > e ? e : mid);
                 const int a = sub == 0 ? s : mid, b = sub == 0 ? mid : e;
-                acc = csr_lane_range<V, T, (UNROLL >= 4 ? 2 : 1)>(a, b, colidx, vals, x);
+                acc = csr_lane_range<V, T, (UNROLL >= 4 ? 2 : 1), GW>(a, b, colidx, vals, x);
             }
         } else if (!skip) {
             for (int k = s + sub; k < e; k += TPR * UNROLL) {
@@ -126,7 +158,10 @@ __device__ __forceinline__ void csr_vector_rows(int64_t base, int64_t m, const i
     }
 }
 
-template <typename V, typename T, int TPR, int UNROLL, int REGCAP>
+// GW: entries per lane load with one or two lanes per row (4: 16-byte
+// loads, 8: 32-byte loads; wider groups read fewer load instructions per
+// entry but mask more slots at a lane's first and last group)
+template <typename V, typename T, int TPR, int UNROLL, int REGCAP, int GW>
 __global__ void __launch_bounds__(1024) __maxnreg__(REGCAP)
 k_csr_vector(int64_t m, const int *__restrict__ rowptr, const int *__restrict__ colidx,
              const V *__restrict__ vals, const T *__restrict__ x, T *__restrict__ y, T alpha, T beta,
@@ -135,7 +170,7 @@ k_csr_vector(int64_t m, const int *__restrict__ rowptr, const int *__restrict__ 
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t base = warp * 32; base < m; base += nwarps * 32)
-        csr_vector_rows<V, T, TPR, UNROLL>(base, m, rowptr, colidx, vals, x, y, ep, long_threshold);
+        csr_vector_rows<V, T, TPR, UNROLL, GW>(base, m, rowptr, colidx, vals, x, y, ep, long_threshold);
 }
 
 // Long CSR rows: one thread block per segment of a long row; segments of one

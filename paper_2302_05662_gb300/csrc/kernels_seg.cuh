@@ -1,16 +1,19 @@
 // Nonzero-balanced SpMV kernels: COO (segmented reduction over row-sorted
-// triplets), the COO part of HYB (accumulating into y), and split CSR
-// (fixed nonzero chunks whose rows are recovered from the row pointers).
+// triplets), the COO part of HYB (accumulating into y), and split CSR in two
+// forms -- warp chunks whose rows are recovered by merging the row pointers
+// with the chunk's positions, and nonzero tiles staged through shared memory
+// by bulk copies.
 //
-// All three cut the nonzeros into chunks of 32*ITEMS entries, one warp per
-// chunk and ITEMS consecutive entries per lane, so a power-law row (the load
-// imbalance the paper notes for CSR in Section 2.3) costs no more than the
-// same number of nonzeros spread over short rows.  Each lane sums its runs
-// of equal rows sequentially, a shuffle-based segmented scan joins runs
-// that cross lanes, and a row that crosses chunks is finished by whichever
-// of its chunks arrives last (an atomic counter per row, no waiting): that
-// warp adds the chunks' partial sums in chunk order, so results do not
-// depend on scheduling.  Counters reset themselves for the next product.
+// COO and the warp chunks cut the nonzeros into chunks of 32*ITEMS entries,
+// one warp per chunk and ITEMS consecutive entries per lane, so a power-law
+// row (the load imbalance the paper notes for CSR in Section 2.3) costs no
+// more than the same number of nonzeros spread over short rows.  Each lane
+// sums its runs of equal rows sequentially, a shuffle-based segmented scan
+// joins runs that cross lanes, and a row that crosses chunks is finished by
+// whichever of its chunks arrives last (an atomic counter per row, no
+// waiting): that warp adds the chunks' partial sums in chunk order, so
+// results do not depend on scheduling.  Counters reset themselves for the
+// next product.
 #pragma once
 
 #include <climits>
@@ -37,16 +40,18 @@ __device__ __forceinline__ void seg_arrive(int64_t row, int64_t c, int64_t c0, i
 
 // Loads ITEMS consecutive entries of lane range [a, a+cnt): values, the
 // gathered x entries and (for COO) rows.  Full chunks use 16-byte vector
-// loads.  Products are formed later by one fused multiply-add per entry.
-template <typename V, typename T, int ITEMS, bool HAS_ROWS>
+// loads, or 32-byte loads with WIDE (arrays the library allocated, whose
+// chunks start on 32-byte boundaries).  Products are formed later by one
+// fused multiply-add per entry.
+template <typename V, typename T, int ITEMS, bool HAS_ROWS, bool WIDE = false>
 __device__ __forceinline__ void seg_load(bool full, int64_t a, int cnt, const int *rows, const int *cols,
                                          const V *vals, const T *x, int (&r)[ITEMS], T (&v)[ITEMS],
                                          T (&xv)[ITEMS]) {
     if (full) {
         int cc[ITEMS];
-        if (HAS_ROWS) ld_idx_vec<ITEMS>(rows + a, r);
-        ld_idx_vec<ITEMS>(cols + a, cc);
-        ld_vals_vec<ITEMS>(vals + a, v);
+        if (HAS_ROWS) ld_idx_vec<ITEMS, WIDE>(rows + a, r);
+        ld_idx_vec<ITEMS, WIDE>(cols + a, cc);
+        ld_vals_vec<ITEMS, WIDE>(vals + a, v);
 #pragma unroll
         for (int j = 0; j < ITEMS; ++j) xv[j] = ld_x(x, cc[j]);
     } else {
@@ -97,8 +102,10 @@ __device__ __forceinline__ T seg_carry(bool need, T fs, T pval) {
 // ---------------------------------------------------------------------------
 // 16 items per lane need more than 64 registers: those variants are limited
 // to 512-thread blocks.
-template <typename V, typename T, int ITEMS, bool ACCUM>
-__global__ void __launch_bounds__(ITEMS >= 16 ? 512 : 1024)
+// WIDE: 32-byte loads (the handle's own arrays); the allocation-free entry
+// point runs on caller arrays aligned to 16 bytes only
+template <typename V, typename T, int ITEMS, bool ACCUM, bool WIDE = false>
+__global__ void __launch_bounds__(ITEMS >= 16 ? 512 : 1024) __maxnreg__(ITEMS >= 16 ? 128 : 64)
 k_coo_seg(int64_t nnz, int64_t m, const int *__restrict__ rows, const int *__restrict__ cols,
           const V *__restrict__ vals, const T *__restrict__ x, T *__restrict__ y, T alpha, T beta,
           const int *__restrict__ meta0, const int *__restrict__ meta1, const PartialsT<T> P) {
@@ -115,7 +122,7 @@ k_coo_seg(int64_t nnz, int64_t m, const int *__restrict__ rows, const int *__res
         const int last_lane = (int)((E1 - E0 - 1) / ITEMS);
         int r[ITEMS];
         T v[ITEMS], xv[ITEMS];
-        seg_load<V, T, ITEMS, true>(E1 - E0 == C, a, cnt, rows, cols, vals, x, r, v, xv);
+        seg_load<V, T, ITEMS, true, WIDE>(E1 - E0 == C, a, cnt, rows, cols, vals, x, r, v, xv);
 
         // row after this lane's range: next lane's first row, or the next
         // chunk's first row (m past the last entry)
@@ -169,103 +176,6 @@ k_coo_seg(int64_t nnz, int64_t m, const int *__restrict__ rows, const int *__res
             // the open row at the chunk end (cur == nr) continues into the next chunk
             const int64_t c0 = (cur == H && h_back) ? hc0 : c;
             seg_arrive<T, ACCUM>(cur, c, c0, tc1, sc, P, y, ep);
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Split CSR: chunks of C nonzeros; meta0[c] = row holding entry c*C,
-// meta0[nchunks] = m-1.  Lanes find their start row by binary search in the
-// row pointers and walk them, so empty rows are written on the way.
-// csr_split_chunk processes chunk c with the whole warp; k_csr_split runs
-// it over all chunks, the batched kernel over its work list.
-// ---------------------------------------------------------------------------
-template <typename V, typename T, int ITEMS>
-__device__ __forceinline__ void csr_split_chunk(int64_t c, int64_t nnz, int64_t m, const int *__restrict__ rowptr,
-                                                const int *__restrict__ cols, const V *__restrict__ vals,
-                                                const T *__restrict__ x, T *__restrict__ y, const Epi<T> &ep,
-                                                const int *__restrict__ meta0, const PartialsT<T> &P) {
-    constexpr int C = 32 * ITEMS;
-    const int lane = threadIdx.x & 31;
-    const int64_t E0 = c * C, E1 = (E0 + C < nnz) ? E0 + C : nnz;
-    const int64_t a = E0 + (int64_t)lane * ITEMS;
-    const int cnt = E1 - a <= 0 ? 0 : (E1 - a >= ITEMS ? ITEMS : (int)(E1 - a));
-    const int last_lane = (int)((E1 - E0 - 1) / ITEMS);
-    int r_unused[ITEMS];
-    T v[ITEMS], xv[ITEMS];
-    seg_load<V, T, ITEMS, false>(E1 - E0 == C, a, cnt, nullptr, cols, vals, x, r_unused, v, xv);
-    const int H = __ldg(meta0 + c);
-    // Row pointers rowptr[H .. H+32] of the chunk's first rows, staged per
-    // warp in shared memory with one coalesced load: the start-row search
-    // and the walk over short or empty rows read them from there.
-    __shared__ int s_win[32][33];
-    int *win = s_win[threadIdx.x >> 5];
-    __syncwarp();  // the previous chunk's reads of the window are done
-    if ((int64_t)H + lane <= m) win[lane] = __ldg(rowptr + H + lane);
-    if (lane == 0 && (int64_t)H + 32 <= m) win[32] = __ldg(rowptr + H + 32);
-    __syncwarp();
-    // rows before H (the empty rows that lane 0 of chunk 0 walks from row 0)
-    // and rows past the window come from global memory
-    auto rp = [&](int64_t r) -> int {
-        const int64_t d = r - H;
-        return d >= 0 && d <= 32 ? win[d] : __ldg(rowptr + r);
-    };
-    int cur = 0;
-    if (cnt > 0 && a > 0) {  // largest row r in [H, H_next] with rowptr[r] <= a
-        int lo = H, hi = __ldg(meta0 + c + 1);
-        while (lo < hi) {
-            const int mid = lo + ((hi - lo + 1) >> 1);  // lo + hi overflows int past 2^30 rows
-            if (rp(mid) <= a) lo = mid; else hi = mid - 1;
-        }
-        cur = lo;
-    }
-    const int fr = cur;
-    int next_end = cnt > 0 ? rp(cur + 1) : 0;
-    T fs = T(0), acc = T(0);
-    bool fflush = false;
-    if (cnt > 0) {
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            if (j < cnt) {
-                while (a + j >= next_end) {
-                    if (!fflush) { fs = acc; fflush = true; }
-                    else seg_write<T, false>(y, cur, acc, ep);
-                    acc = T(0);
-                    ++cur;
-                    next_end = rp(cur + 1);
-                }
-                acc = fma(v[j], xv[j], acc);
-            }
-        }
-        const int64_t b = a + cnt;
-        while (cur < m && next_end <= b) {
-            if (!fflush) { fs = acc; fflush = true; }
-            else seg_write<T, false>(y, cur, acc, ep);
-            acc = T(0);
-            ++cur;
-            if (cur < m) next_end = rp(cur + 1);
-        }
-    }
-    const int key = (cnt > 0 && cur < m) ? cur : -1;
-    const T sc = seg_scan<T>(key, key >= 0 ? acc : T(0));
-    const int pkey = __shfl_up_sync(0xffffffffu, key, 1);
-    const T pval = __shfl_up_sync(0xffffffffu, sc, 1);
-    const int hstart = rp(H);
-    const bool h_back = hstart < E0;
-    const T total = seg_carry<T>(cnt > 0 && fflush && lane > 0 && pkey == fr, fs, pval);
-    if (cnt > 0 && fflush) {
-        if (fr == H && h_back) {
-            const int64_t c0 = hstart / C, c1 = (rp(H + 1) - 1) / C;
-            seg_arrive<T, false>(fr, c, c0, c1, total, P, y, ep);
-        } else {
-            seg_write<T, false>(y, fr, total, ep);
-        }
-    }
-    if (lane == last_lane && cur < m) {
-        const int s0 = rp(cur);
-        if (s0 < E1 && next_end > E1) {  // open row continues into the next chunk
-            const int64_t c0 = s0 / C, c1 = (next_end - 1) / C;
-            seg_arrive<T, false>(cur, c, c0, c1, sc, P, y, ep);
         }
     }
 }
@@ -513,18 +423,196 @@ k_csr_tiles(int64_t nnz, int64_t m, int64_t ntiles, int tile, int long_len, int 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Split CSR by warp chunks: the nonzeros cut into chunks of C = 32 ITEMS
+// entries, one warp per chunk, ITEMS consecutive entries per lane loaded as
+// COO loads them but without a row index per entry -- the warp recovers the
+// rows by merging the row pointers with the chunk's positions.
+//
+// meta[c] = first row r with rowptr[r] >= c C (meta[nchunks] = m), so the
+// rows [meta[c], meta[c+1]) start inside chunk c (the last chunk also holds
+// the empty rows at the end), and row meta[c] - 1 may continue into it from
+// before.  A rows pass reads those row pointers 32 rows at a time (coalesced
+// loads), writes the empty rows among them, and lists the rows that have
+// entries in the chunk, in order: list index k -> row id in `lr`, and the
+// position inside the chunk where row k starts sets a bit of `bits`.  A lane
+// finds the list index of its first entry's row by counting the set bits up
+// to its first position, and walks its entries, moving to the next list row
+// at each set bit -- one integer test per entry, no search.  Runs that cross
+// lanes are joined by the same segmented scan as COO (keyed by list index),
+// and a row crossing chunks by the same fixed-order partials.
+// ---------------------------------------------------------------------------
+template <int ITEMS>
+struct MergeSmem {
+    int lr[32 * ITEMS];     // row id of each list index
+    unsigned bits[ITEMS];   // bit p: a listed row starts at chunk position p
+};
+
 template <typename V, typename T, int ITEMS>
-__global__ void __launch_bounds__(ITEMS >= 16 ? 512 : 1024)
-k_csr_split(int64_t nnz, int64_t m, const int *__restrict__ rowptr, const int *__restrict__ cols,
+__device__ __forceinline__ void csr_merge_chunk(int64_t c, int64_t nnz, int64_t m, const int *__restrict__ rowptr,
+                                                const int *__restrict__ cols, const V *__restrict__ vals,
+                                                const T *__restrict__ x, T *__restrict__ y, const Epi<T> &ep,
+                                                int m0, int m1, const PartialsT<T> &P,
+                                                MergeSmem<ITEMS> &W) {
+    static_assert(32 % ITEMS == 0, "a lane's positions must sit in one word of the bitmap");
+    constexpr int C = 32 * ITEMS;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    // offsets and rows fit in 32 bits: a handle holds fewer than 2^31 nonzeros
+    const int E0 = (int)(c * C), E1 = (int)((c * C + C < nnz) ? c * C + C : nnz);
+    const int n = E1 - E0;
+    const int pos = lane * ITEMS;
+    const int cnt = n - pos <= 0 ? 0 : (n - pos >= ITEMS ? ITEMS : n - pos);
+    const int last_lane = (n - 1) / ITEMS;
+    // rows [rb, m1) are read 32 at a time (rb < m1: row m1 - 1 holds or
+    // follows entry E1 - 1); the first 32 row pointers are loaded before the
+    // entries so that both latencies overlap
+    const int rb = m0 > 0 ? m0 - 1 : 0;
+    const bool v1 = rb + lane < m1;
+    const int s1 = v1 ? __ldg(rowptr + rb + lane) : 0;
+    const int e1 = v1 ? __ldg(rowptr + rb + lane + 1) : 0;
+    int r_unused[ITEMS];
+    T v[ITEMS], xv[ITEMS];
+    seg_load<V, T, ITEMS, false, true>(n == C, (int64_t)E0 + pos, cnt, nullptr, cols, vals, x, r_unused, v, xv);
+
+    // rows pass
+    __syncwarp();  // the previous chunk's reads of W are done
+    if (lane < ITEMS) W.bits[lane] = 0u;
+    __syncwarp();
+    int K = 0;
+    int hs = 0, he = 0, te = 0;  // head row's start and end, tail row's end (whole rows)
+    auto round = [&](int r0, int s, int e) {
+        const int r = r0 + lane;
+        const bool valid = r < m1;
+        if (valid && s == e && r >= m0) ep.store(y, (int64_t)r, T(0));
+        const int cs = s > E0 ? s : E0, ce = e < E1 ? e : E1;
+        const bool in = valid && cs < ce;
+        const unsigned bal = __ballot_sync(FULL, in);
+        if (bal) {  // warp-uniform
+            if (in) {
+                const int k = K + __popc(bal & ((1u << lane) - 1u));
+                W.lr[k] = r;
+                const int p = cs - E0;
+                atomicOr(&W.bits[p >> 5], 1u << (p & 31));
+            }
+            const int f = __ffs(bal) - 1, l = 31 - __clz(bal);
+            if (K == 0) {
+                hs = __shfl_sync(FULL, s, f);
+                he = __shfl_sync(FULL, e, f);
+            }
+            te = __shfl_sync(FULL, e, l);
+            K += __popc(bal);
+        }
+    };
+    round(rb, s1, e1);
+    // chunks of short rows span many rows: the row pointers of up to four
+    // rounds are loaded together
+    constexpr int RB = 4;
+    for (int r0 = rb + 32; r0 < m1; r0 += 32 * RB) {
+        int sv[RB], ev[RB];
+#pragma unroll
+        for (int q = 0; q < RB; ++q) {
+            const int r = r0 + 32 * q + lane;
+            sv[q] = r < m1 ? __ldg(rowptr + r) : 0;
+            ev[q] = r < m1 ? __ldg(rowptr + r + 1) : 0;
+        }
+#pragma unroll
+        for (int q = 0; q < RB; ++q)
+            if (r0 + 32 * q < m1) round(r0 + 32 * q, sv[q], ev[q]);
+    }
+    __syncwarp();
+
+    // list index of the row holding this lane's first entry: set bits in
+    // positions [0, pos], minus one (position 0 always starts list row 0)
+    const int w = pos >> 5, b = pos & 31;
+    const int pc = lane < ITEMS ? __popc(W.bits[lane]) : 0;
+    int incl = pc;
+#pragma unroll
+    for (int d = 1; d < ITEMS; d <<= 1) {
+        const int t = __shfl_up_sync(FULL, incl, d);
+        if (lane >= d) incl += t;
+    }
+    const int before = __shfl_sync(FULL, incl - pc, w);  // set bits in words before w
+    const unsigned word = W.bits[w];
+    const int k0 = before + __popc(word & ((2u << b) - 1u)) - 1;
+    const unsigned mb = ITEMS == 32 ? (word >> b) : ((word >> b) & ((1u << ITEMS) - 1u));
+
+    int cur = k0;
+    const int fr = k0;
+    T fs = T(0), acc = T(0);
+    bool fflush = false;
+    if (cnt > 0) {
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            if (j < cnt) {
+                if (j > 0 && ((mb >> j) & 1u)) {  // entry pos + j starts the next list row
+                    if (!fflush) { fs = acc; fflush = true; }
+                    else seg_write<T, false>(y, W.lr[cur], acc, ep);
+                    ++cur;
+                    acc = T(0);
+                }
+                acc = fma(v[j], xv[j], acc);
+            }
+        }
+    }
+    // list row after this lane's range: the next lane's first row; after
+    // the chunk's last entry, the tail row again if it continues past E1,
+    // else K (no row)
+    const int k0n = __shfl_down_sync(FULL, k0, 1);
+    const bool t_fwd = te > E1;
+    const int nr = lane == last_lane ? (t_fwd ? K - 1 : K) : k0n;
+    if (cnt > 0 && nr != cur) {  // the lane's last row ends exactly at its end
+        if (!fflush) { fs = acc; fflush = true; }
+        else seg_write<T, false>(y, W.lr[cur], acc, ep);
+        cur = nr;
+        acc = T(0);
+    }
+    const int key = cnt > 0 ? cur : -1;
+    const T sc = seg_scan<T>(key, cnt > 0 ? acc : T(0));
+    const int pkey = __shfl_up_sync(FULL, key, 1);
+    const T pval = __shfl_up_sync(FULL, sc, 1);
+    const bool h_back = hs < E0;  // list row 0 started in an earlier chunk
+    const T total = seg_carry<T>(cnt > 0 && fflush && lane > 0 && pkey == fr, fs, pval);
+    if (cnt > 0 && fflush) {
+        if (fr == 0 && h_back)
+            seg_arrive<T, false>(W.lr[0], c, hs / C, (he - 1) / C, total, P, y, ep);
+        else
+            seg_write<T, false>(y, W.lr[fr], total, ep);
+    }
+    if (lane == last_lane && t_fwd) {  // the tail row continues into the next chunk
+        const int64_t c0 = (cur == 0 && h_back) ? hs / C : c;
+        seg_arrive<T, false>(W.lr[cur], c, c0, (te - 1) / C, sc, P, y, ep);
+    }
+}
+
+// one MergeSmem per warp in dynamic shared memory; 16 items per lane need
+// more than 64 registers, so those variants take at most 512 threads per
+// block
+template <typename V, typename T, int ITEMS>
+__global__ void __launch_bounds__(ITEMS >= 16 ? 512 : 1024) __maxnreg__(ITEMS >= 16 ? 128 : 64)
+k_csr_merge(int64_t nnz, int64_t m, const int *__restrict__ rowptr, const int *__restrict__ cols,
             const V *__restrict__ vals, const T *__restrict__ x, T *__restrict__ y, T alpha, T beta,
-            const int *__restrict__ meta0, const PartialsT<T> P) {
+            const int *__restrict__ meta, const PartialsT<T> P) {
+    extern __shared__ __align__(16) unsigned char merge_smem[];
+    MergeSmem<ITEMS> &W = reinterpret_cast<MergeSmem<ITEMS> *>(merge_smem)[threadIdx.x >> 5];
     const Epi<T> ep(alpha, beta);
     constexpr int C = 32 * ITEMS;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t nchunks = (nnz + C - 1) / C;
-    for (int64_t c = warp; c < nchunks; c += nwarps)
-        csr_split_chunk<V, T, ITEMS>(c, nnz, m, rowptr, cols, vals, x, y, ep, meta0, P);
+    // each chunk's row range is loaded one chunk ahead
+    int m0 = 0, m1 = 0;
+    if (warp < nchunks) {
+        m0 = __ldg(meta + warp);
+        m1 = __ldg(meta + warp + 1);
+    }
+    for (int64_t c = warp; c < nchunks; c += nwarps) {
+        const int64_t cn = c + nwarps;
+        const int n0 = cn < nchunks ? __ldg(meta + cn) : 0, n1 = cn < nchunks ? __ldg(meta + cn + 1) : 0;
+        csr_merge_chunk<V, T, ITEMS>(c, nnz, m, rowptr, cols, vals, x, y, ep, m0, m1, P, W);
+        m0 = n0;
+        m1 = n1;
+    }
 }
 
 }  // namespace spmv

@@ -53,9 +53,9 @@ int launch_bsr_long(const spmv_matrix *h, T alpha, const T *x, T beta, T *y, cud
 }
 
 // ------------------------------- CSR vector --------------------------------
-template <typename V, typename T, int TPR, int U, int RC>
+template <typename V, typename T, int TPR, int U, int RC, int GW>
 int launch_csr_vector(const spmv_matrix *h, T alpha, const T *x, T beta, T *y, cudaStream_t s) {
-    auto kern = k_csr_vector<V, T, TPR, U, RC>;
+    auto kern = k_csr_vector<V, T, TPR, U, RC, GW>;
     const int tpb = h->cfg.threads_per_block;
     SPMV_TRY(apply_carveout((const void *)kern, h->cfg.carveout));
     const int64_t rows_per_block = tpb / TPR;
@@ -66,10 +66,17 @@ int launch_csr_vector(const spmv_matrix *h, T alpha, const T *x, T beta, T *y, c
     return launch_csr_long<V, T>(h, alpha, x, beta, y, s);
 }
 
+// bsr_block selects the load group of one or two lanes per row: 8 entries
+// (32-byte loads) or 4; more lanes per row read interleaved entries
 template <typename V, typename T, int TPR, int U>
 int csr_vector_rc(const spmv_matrix *h, T a, const T *x, T b, T *y, cudaStream_t s) {
-    return h->cfg.regcap == 32 ? launch_csr_vector<V, T, TPR, U, 32>(h, a, x, b, y, s)
-                               : launch_csr_vector<V, T, TPR, U, 64>(h, a, x, b, y, s);
+    if constexpr (TPR <= 2) {
+        if (h->cfg.bsr_block == 8)
+            return h->cfg.regcap == 32 ? launch_csr_vector<V, T, TPR, U, 32, 8>(h, a, x, b, y, s)
+                                       : launch_csr_vector<V, T, TPR, U, 64, 8>(h, a, x, b, y, s);
+    }
+    return h->cfg.regcap == 32 ? launch_csr_vector<V, T, TPR, U, 32, 4>(h, a, x, b, y, s)
+                               : launch_csr_vector<V, T, TPR, U, 64, 4>(h, a, x, b, y, s);
 }
 
 template <typename V, typename T, int TPR>
@@ -231,7 +238,7 @@ int run_sell_vt(const spmv_matrix *h, double alpha, const void *x, double beta, 
 template <typename V, typename T, int ITEMS, bool ACCUM>
 int launch_coo(const spmv_matrix *h, int64_t nnz, const int *rows, const int *cols, const V *vals, T alpha,
                const T *x, T beta, T *y, cudaStream_t s) {
-    auto kern = k_coo_seg<V, T, ITEMS, ACCUM>;
+    auto kern = k_coo_seg<V, T, ITEMS, ACCUM, true>;
     const int tpb = ITEMS >= 16 && h->cfg.threads_per_block > 512 ? 512 : h->cfg.threads_per_block;
     SPMV_TRY(apply_carveout((const void *)kern, h->cfg.carveout));
     const int64_t chunks = (nnz + 32 * ITEMS - 1) / (32 * ITEMS);
@@ -316,11 +323,37 @@ int tiles_tpr(const spmv_matrix *h, T a, const T *x, T b, T *y, cudaStream_t s) 
     }
 }
 
+// split CSR by warp chunks: one MergeSmem per warp in dynamic shared memory
+template <typename V, typename T, int ITEMS>
+int launch_merge(const spmv_matrix *h, T alpha, const T *x, T beta, T *y, cudaStream_t s) {
+    auto kern = k_csr_merge<V, T, ITEMS>;
+    const int tpb = ITEMS >= 16 && h->cfg.threads_per_block > 512 ? 512 : h->cfg.threads_per_block;
+    const size_t smem = sizeof(MergeSmem<ITEMS>) * (size_t)(tpb / 32);
+    if (smem > 48 * 1024)
+        SPMV_CUDA_TRY(cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SPMV_TRY(apply_carveout((const void *)kern, h->cfg.carveout));
+    const int64_t chunks = h->seg.nchunks;
+    const int64_t wpb = tpb / 32;
+    const int64_t cap = (int64_t)resident_blocks_smem((const void *)kern, tpb, smem) * h->sm_count;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((chunks + wpb - 1) / wpb, cap));
+    kern<<<grid, tpb, smem, s>>>(h->nnz, h->m, h->rowptr, h->colidx, (const V *)h->vals, x, y, alpha, beta,
+                                 h->seg.meta0, PartialsT<T>::of(h->seg.part));
+    SPMV_LAUNCH_CHECK();
+    return SPMV_OK;
+}
+
 template <int VT>
 int run_csr_split_vt(const spmv_matrix *h, double alpha, const void *x, double beta, void *y, cudaStream_t s) {
     using V = typename VT_<VT>::V;
     using T = typename VT_<VT>::T;
     const T a = (T)alpha, b = (T)beta;
+    if (h->cfg.hyb_ell_width == 0) {
+        switch (h->seg.items) {
+        case 4: return launch_merge<V, T, 4>(h, a, (const T *)x, b, (T *)y, s);
+        case 8: return launch_merge<V, T, 8>(h, a, (const T *)x, b, (T *)y, s);
+        default: return launch_merge<V, T, 16>(h, a, (const T *)x, b, (T *)y, s);
+        }
+    }
     if (h->cfg.unroll >= 4) return tiles_tpr<V, T, 8>(h, a, (const T *)x, b, (T *)y, s);
     return tiles_tpr<V, T, 4>(h, a, (const T *)x, b, (T *)y, s);
 }

@@ -52,10 +52,19 @@ def label_space(tpb=TPB, include_sell: bool = False):
 
 def refine_space(best: dict):
     """Register cap x unroll x carveout around a winning point (x SELL's
-    column groups: column-major or groups of four)."""
+    column groups: column-major or groups of four; x split CSR's form: warp
+    chunks, or staged tiles of 1024 or 4096 nonzeros; x vector CSR's load
+    group of 4 or 8 entries)."""
     out = []
     ell_family = best.get("format", 0) in (B.FMT_ELL, B.FMT_HYB, B.FMT_SELL)
-    groups = (1, 4) if best.get("format", 0) == B.FMT_SELL else (None,)   # SELL column groups
+    if best.get("format", 0) == B.FMT_SELL:
+        groups = [("bsr_block", 1), ("bsr_block", 4)]             # SELL column groups
+    elif best.get("format", 0) == B.FMT_CSR and best.get("threads_per_row") == B.TPR_SPLIT:
+        groups = [("hyb_ell_width", w) for w in (0, 1024, 4096)]  # split CSR form
+    elif best.get("format", 0) == B.FMT_CSR and best.get("threads_per_row", 0) in (0, 1, 2):
+        groups = [("bsr_block", 4), ("bsr_block", 8)]             # CSR load group (1-2 lanes per row)
+    else:
+        groups = [None]
     for rc in ((32, 48, 64) if ell_family else (32, 64)):
         for u in ((1, 2, 4, 8) if ell_family else (1, 2, 4)):
             for cv in (-1, 0, 100):
@@ -63,7 +72,7 @@ def refine_space(best: dict):
                     d = dict(best)
                     d.update(regcap=rc, unroll=u, carveout=cv)
                     if g is not None:
-                        d["bsr_block"] = g
+                        d[g[0]] = g[1]
                     out.append(d)
     return out
 

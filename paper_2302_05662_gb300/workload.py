@@ -10,7 +10,8 @@ from . import binding as B
 # (name, spmv_config fields) of the format sweep over the five matrices
 SWEEP_VARIANTS = (
     ("csr", dict(format=B.FMT_CSR)),                                  # vector CSR, tpr from mean row length
-    ("csr_split", dict(format=B.FMT_CSR, threads_per_row=B.TPR_SPLIT)),  # nnz-balanced CSR
+    ("csr_split", dict(format=B.FMT_CSR, threads_per_row=B.TPR_SPLIT)),  # nnz-balanced CSR: warp chunks
+    ("csr_tiles", dict(format=B.FMT_CSR, threads_per_row=B.TPR_SPLIT, hyb_ell_width=4096)),  # staged tiles
     ("ell", dict(format=B.FMT_ELL)),
     ("coo", dict(format=B.FMT_COO)),
     ("hyb", dict(format=B.FMT_HYB)),

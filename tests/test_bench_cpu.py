@@ -22,6 +22,7 @@ def test_byte_model_counts_the_format_independent_bytes():
 def test_format_names():
     import bench
     assert bench.fmt_name({"format": 0, "threads_per_row": -1}) == "csr_split"
+    assert bench.fmt_name({"format": 0, "threads_per_row": -1, "hyb_ell_width": 4096}) == "csr_tiles"
     assert bench.fmt_name({"format": 0, "threads_per_row": 4}) == "csr"
     assert [bench.fmt_name({"format": f}) for f in range(1, 6)] == ["ell", "coo", "hyb", "bsr", "sell"]
 

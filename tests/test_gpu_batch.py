@@ -105,6 +105,31 @@ def test_batch_run_one_shot_integer_exact(oracle):
             B.spmv_destroy(h)
 
 
+def test_batch_of_more_matrices_than_shared_memory_offsets(oracle):
+    """4200 small matrices: past 4095 the kernel searches the item offsets
+    in global memory instead of shared memory; integer inputs, exact."""
+    import torch
+    rng = np.random.default_rng(11)
+    mats = []
+    for i in range(4200):
+        n = int(rng.integers(1, 90))
+        nnz = int(rng.integers(0, 4 * n + 1))
+        coo = matgen.random_coo(n, n, nnz, np.random.default_rng(5000 + i))
+        coo.vals = rng.integers(-4, 5, size=coo.nnz).astype(np.float64)
+        mats.append(coo)
+    hs = [create(c, B.SPMV_F64) for c in mats]
+    xs = [torch.from_numpy(matgen.dense_vector(c.n, k, integer_values=5)).cuda() for k, c in enumerate(mats)]
+    ys = [torch.full((c.m,), 7.0, dtype=torch.float64, device="cuda") for c in mats]
+    try:
+        B.spmv_batch_run(hs, np.ones(len(mats)), xs, np.full(len(mats), -1.0), ys)
+        for k, c in enumerate(mats):
+            want = oracle.spmv_coo_obj(c, xs[k].cpu().numpy()) - 7.0
+            assert np.array_equal(ys[k].cpu().numpy(), want), k
+    finally:
+        for h in hs:
+            B.spmv_destroy(h)
+
+
 def test_batch_rejects_mixed_types():
     import torch
     a = matgen.laplacian_2d(8)

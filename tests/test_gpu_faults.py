@@ -27,6 +27,7 @@ MIB = 1 << 20
 FORMATS = [
     ("csr", dict(format=B.FMT_CSR)),
     ("csr_split", dict(format=B.FMT_CSR, threads_per_row=B.TPR_SPLIT)),
+    ("csr_tiles", dict(format=B.FMT_CSR, threads_per_row=B.TPR_SPLIT, hyb_ell_width=4096)),
     ("ell", dict(format=B.FMT_ELL)),
     ("coo", dict(format=B.FMT_COO)),
     ("hyb", dict(format=B.FMT_HYB)),

@@ -115,6 +115,7 @@ LAUNCH_CASES = (
     [("csr", dict(threads_per_row=t, unroll=u, regcap=rc))
      for t in (1, 2, 4, 8, 16, 32) for u in (1, 2, 4) for rc in (32, 64)]
     + [("csr_split", dict(unroll=u)) for u in (1, 2, 4)]
+    + [("csr_split", dict(hyb_ell_width=w, unroll=u)) for w in (256, 1024, 8192) for u in (2, 4)]
     + [(nm, dict(unroll=u, regcap=rc)) for nm in ("ell", "hyb", "sell")
        for u in (1, 2, 4, 8) for rc in (32, 48, 64)]
     + [("coo", dict(unroll=u)) for u in (1, 2, 4)]
@@ -397,7 +398,7 @@ def test_ell_width_limit_reported():
     assert ei.value.status == -4
 
 
-@pytest.mark.parametrize("name", ["coo", "csr_split", "hyb"])
+@pytest.mark.parametrize("name", ["coo", "csr_split", "csr_tiles", "hyb"])
 def test_repeated_runs_bitwise_identical(oracle, name):
     """The cross-chunk counters reset themselves: back-to-back products on
     one handle give identical bits (sums in a fixed order)."""
