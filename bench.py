@@ -446,6 +446,7 @@ def batched_section(B, matgen, torch, count=512, seed=7, steps=20, select=True):
             "formats_selected": fmts,
             "plan": {"items": items, "threads_per_block": tpb,
                      "ell_matrices": int((modes == -1).sum()), "sell_matrices": int((modes == -5).sum()),
+                     "coo_matrices": int((modes == -2).sum()), "bsr_matrices": int((modes == -4).sum()),
                      "csr_split_matrices": int((modes == 0).sum()),
                      "csr_vector_matrices": int((modes > 0).sum())}}
 

@@ -386,9 +386,12 @@ SPMV_API int spmv_select(spmv_handle h, spmv_config *out_cfg, double *h_features
  * work items over all matrices that a grid of resident thread blocks
  * consumes through one atomic counter.  A matrix whose handle holds ELL or
  * SELL runs in that format (ELL: 32 rows per item, a row per lane; SELL:
- * the handle's work items; mode -1 and -5); any other handle runs from its
- * CSR arrays as nonzero chunks of 32*items entries per warp (split, mode 0)
- * or 32-row groups with 1..32 lanes per row (vector, mode = lanes per row).
+ * the handle's work items; mode -1 and -5), a COO handle as COO chunks of
+ * 32*items entries per warp (mode -2) and a BSR handle as groups of 32 / r
+ * block rows with r lanes each (mode -4), unless the tuner finds a CSR mode
+ * faster; any other handle runs from its CSR arrays as nonzero chunks of
+ * 32*items entries per warp (split, mode 0) or 32-row groups with 1..32
+ * lanes per row (vector, mode = lanes per row).
  * The counter reset and the kernel are captured in a CUDA graph.
  *
  * spmv_batch_create: hs[i] (all of one value type), alpha[i], beta[i] (host
@@ -397,13 +400,15 @@ SPMV_API int spmv_select(spmv_handle h, spmv_config *out_cfg, double *h_features
  * scratch): the handles and vectors must outlive the plan, keep their
  * addresses and formats, and not run other products while the plan does.  Default modes come from
  * row-length statistics.  Synchronises `stream`.
- * spmv_batch_tune: autotuner -- times every CSR mode per CSR matrix on
- * one-matrix launches, then the chunk size (items 4/8/16) and block size
+ * spmv_batch_tune: autotuner -- times every CSR mode (and COO chunks or BSR
+ * block rows for a COO or BSR handle) per matrix, each on one launch over enough copies of the
+ * matrix to fill the GPU (about 4M entries), then the chunk size (items 4/8/16) and block size
  * (128/256/512) on the whole batch, keeps the fastest and re-captures the
  * graph.  Overwrites y.  Synchronises `stream`.
  * spmv_batch_launch: replays the graph on `stream` (no synchronisation).
  * spmv_batch_get_plan: copies the per-matrix modes (0 = split, lanes per
- * row for vector CSR, -1 ELL, -5 SELL; h_modes may be NULL), the items and
+ * row for vector CSR, -1 ELL, -2 COO chunks, -4 BSR, -5 SELL; h_modes may be
+ * NULL), the items and
  * the block size.
  * spmv_batch_run: create + launch + destroy in one call (synchronises).
  * Errors: SPMV_ERR_INVALID (NULL arrays or handles, mixed value types),

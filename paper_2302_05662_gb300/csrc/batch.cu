@@ -49,8 +49,16 @@ struct BatchMat {
     double alpha, beta;
     int64_t m, nnz;
     int64_t part_off;  // first chunk of this matrix in the batch partials
-    const int *meta0;  // split: first row starting at or after each chunk's first entry
-    int mode;          // CSR: 0 split, else lanes per row
+    const int *meta0;  // split: first row starting at or after each chunk's first entry;
+                       // COO: first chunk of each chunk's head row
+    const int *meta1;  // COO: last chunk of each chunk's tail row
+    const int *coo_rows;  // COO handles: the row index of each entry
+    // BSR: block rows, r x r blocks; n bounds the last block column
+    const int *bsr_rowptr, *bsr_col;
+    const void *bsr_val;
+    int64_t bsr_mb, n;
+    int bsr_r, pad3;
+    int mode;          // CSR: 0 split, -2 COO chunks, else lanes per row
     int fmt;           // the handle's format: SPMV_FMT_ELL, SPMV_FMT_SELL, or CSR (any other)
     // ELL: column-major arrays, int32 columns or 16-bit offsets
     const int *ell_col;
@@ -63,23 +71,55 @@ struct BatchMat {
     const int *sell_col, *sell_perm;
     const void *sell_val;
     int64_t nitems, s_zero;
-    int sell_grouped, pad2;
+    int sell_grouped;
+    int wide;  // CSR vector mode: 8-entry load groups (32-byte loads)
     void *p_head, *p_tail;
     unsigned *p_count;
     unsigned long long *p_xslot;
 };
 
-// work items of one matrix: CSR split chunks or 32-row groups, ELL 32-row
-// groups, SELL items plus 32-row groups of its empty rows
+// mode of a COO handle run as COO chunks (its own row indices), of a BSR
+// handle run as BSR block rows (32 / r block rows per item, r lanes each)
+constexpr int BATCH_COO = -SPMV_FMT_COO;
+constexpr int BATCH_BSR = -SPMV_FMT_BSR;
+
+// work items of one matrix: CSR split or COO chunks, or 32-row groups, ELL
+// 32-row groups, SELL items plus 32-row groups of its empty rows
 int64_t batch_items(const BatchMat &M, int C) {
     if (M.fmt == SPMV_FMT_ELL) return (M.m + 31) / 32;
     if (M.fmt == SPMV_FMT_SELL) return M.nitems + (std::max<int64_t>(0, M.m - 32 * M.s_zero) + 31) / 32;
-    return M.mode == 0 ? (M.nnz + C - 1) / C : (M.m + 31) / 32;
+    if (M.fmt == SPMV_FMT_BSR) return (M.bsr_mb + 32 / M.bsr_r - 1) / (32 / M.bsr_r);
+    return M.mode == 0 || M.mode == BATCH_COO ? (M.nnz + C - 1) / C : (M.m + 31) / 32;
+}
+
+// chunk metadata of a split or COO matrix for chunks of C entries, in one
+// allocation of 2 (nchunks + 1) ints (COO: meta0 then meta1)
+int build_chunk_meta(const spmv_matrix *h, int mode, int C, int32_t **out, cudaStream_t s) {
+    const int64_t nch = (h->nnz + C - 1) / C;
+    *out = nullptr;
+    SPMV_CUDA_TRY(dev_malloc((void **)out, sizeof(int32_t) * 2 * (nch + 1)));
+    return mode == BATCH_COO ? build_coo_meta(h->coo_rows, h->rowptr, h->nnz, C, *out, *out + nch + 1, s)
+                             : build_merge_meta(h->rowptr, h->m, h->nnz, C, *out, s);
+}
+
+void set_chunk_meta(BatchMat &M, const int32_t *meta, int C) {
+    const int64_t nch = (M.nnz + C - 1) / C;
+    M.meta0 = meta;
+    M.meta1 = meta + nch + 1;
 }
 
 // the handle's active format as the batch runs it (ELL, SELL, else CSR modes)
 void describe_format(const spmv_matrix *h, BatchMat &M) {
     M.fmt = SPMV_FMT_CSR;
+    M.coo_rows = h->cfg.format == SPMV_FMT_COO ? h->coo_rows : nullptr;
+    if (h->cfg.format == SPMV_FMT_BSR && h->bsr_rowptr) {
+        M.bsr_rowptr = h->bsr_rowptr;
+        M.bsr_col = h->bsr_col;
+        M.bsr_val = h->bsr_val;
+        M.bsr_mb = h->bsr_mb;
+        M.bsr_r = h->bsr_r;
+    }
+    M.n = h->n;
     if (h->cfg.format == SPMV_FMT_ELL && (h->ell_col || h->ell_d16)) {
         M.fmt = SPMV_FMT_ELL;
         M.ell_col = h->ell_col;
@@ -109,6 +149,14 @@ void describe_format(const spmv_matrix *h, BatchMat &M) {
 }
 
 // register budget: 16 items per lane, or fp64 sums, need more than 64
+// vector mode with one or two lanes per row takes 8-entry load groups once
+// a lane's part of a mean row holds 16 or more entries (the single-matrix
+// default rule)
+int wide_groups(const spmv_matrix *h, int mode) {
+    const double mean = h->m > 0 ? (double)h->nnz / (double)h->m : 0.0;
+    return mode >= 1 && mode <= 2 && mean / mode >= 16.0 ? 1 : 0;
+}
+
 template <typename V, typename T, int ITEMS>
 __global__ void __launch_bounds__(512) __maxnreg__(ITEMS >= 16 ? 128 : (sizeof(T) == 8 ? 96 : 64))
 k_batch(const BatchMat *__restrict__ mats, int count, const int64_t *__restrict__ item_off, int64_t total,
@@ -125,7 +173,7 @@ k_batch(const BatchMat *__restrict__ mats, int count, const int64_t *__restrict_
             const int mid = (lo + hi + 1) >> 1;
             if ((unsigned long long)__ldg(item_off + mid) <= item) lo = mid; else hi = mid - 1;
         }
-        const BatchMat M = mats[lo];
+        const BatchMat &M = mats[lo];  // fields read where a branch needs them
         const int64_t local = (int64_t)item - __ldg(item_off + lo);
         const Epi<T> ep((T)M.alpha, (T)M.beta);
         const V *vals = (const V *)M.vals;
@@ -142,8 +190,8 @@ k_batch(const BatchMat *__restrict__ mats, int count, const int64_t *__restrict_
         } else if (M.fmt == SPMV_FMT_SELL) {
             if (local < M.nitems) {
                 const PartialsT<T> Ps{(T *)M.p_head, (T *)M.p_tail, M.p_count, M.p_xslot, 32};
-                if (M.sell_grouped)
-                    sell_item<V, T, 8, true>(local, M.m, M.it_slice, M.it_base, M.it_len, M.it_c0, M.it_c1,
+                if (M.sell_grouped)  // two groups of four in flight, one with 4 items per lane (register budget)
+                    sell_item<V, T, (ITEMS >= 8 ? 8 : 4), true>(local, M.m, M.it_slice, M.it_base, M.it_len, M.it_c0, M.it_c1,
                                              M.sell_col, (const V *)M.sell_val, M.sell_perm, x, y, ep, Ps);
                 else
                     sell_item<V, T, 4, false>(local, M.m, M.it_slice, M.it_base, M.it_len, M.it_c0, M.it_c1,
@@ -152,21 +200,39 @@ k_batch(const BatchMat *__restrict__ mats, int count, const int64_t *__restrict_
                 const int64_t p = M.s_zero * 32 + (local - M.nitems) * 32 + lane;
                 if (p < M.m) ep.store(y, __ldg(M.sell_perm + p), T(0));
             }
-        } else if (M.mode == 0) {
+        } else if (M.fmt == SPMV_FMT_BSR) {  // 32 / r block rows, r lanes per block row
+            const int big = 0x7fffffff;
+            if (M.bsr_r == 4)
+                bsr_rows<V, T, 4, 1>(local * 8, M.bsr_mb, M.m, M.n, M.bsr_rowptr, M.bsr_col, (const V *)M.bsr_val, x,
+                                     y, ep, big);
+            else
+                bsr_rows<V, T, 2, 1>(local * 16, M.bsr_mb, M.m, M.n, M.bsr_rowptr, M.bsr_col, (const V *)M.bsr_val,
+                                     x, y, ep, big);
+        } else if (M.mode == 0 || M.mode == BATCH_COO) {
             PartialsT<T> Pm = P;
             Pm.head += M.part_off;
             Pm.tail += M.part_off;
             Pm.count += M.part_off;
             Pm.xslot += M.part_off;
-            csr_merge_chunk<V, T, ITEMS>(local, M.nnz, M.m, M.rowptr, M.colidx, vals, x, y, ep, __ldg(M.meta0 + local),
-                                         __ldg(M.meta0 + local + 1), Pm,
-                                         s_merge[threadIdx.x >> 5]);
+            if (M.mode == BATCH_COO)
+                coo_chunk<V, T, ITEMS, false, true>(local, M.nnz, M.m, M.coo_rows, M.colidx, vals, x, y, ep, M.meta0,
+                                                    M.meta1, Pm);
+            else
+                csr_merge_chunk<V, T, ITEMS>(local, M.nnz, M.m, M.rowptr, M.colidx, vals, x, y, ep,
+                                             __ldg(M.meta0 + local), __ldg(M.meta0 + local + 1), Pm,
+                                             s_merge[threadIdx.x >> 5]);
         } else {
             const int64_t base = local * 32;
             const int big = 0x7fffffff;
             switch (M.mode) {
-            case 1: csr_vector_rows<V, T, 1, 2>(base, M.m, M.rowptr, M.colidx, vals, x, y, ep, big); break;
-            case 2: csr_vector_rows<V, T, 2, 2>(base, M.m, M.rowptr, M.colidx, vals, x, y, ep, big); break;
+            case 1:
+                if (M.wide) csr_vector_rows<V, T, 1, 2, 8>(base, M.m, M.rowptr, M.colidx, vals, x, y, ep, big);
+                else csr_vector_rows<V, T, 1, 2>(base, M.m, M.rowptr, M.colidx, vals, x, y, ep, big);
+                break;
+            case 2:
+                if (M.wide) csr_vector_rows<V, T, 2, 2, 8>(base, M.m, M.rowptr, M.colidx, vals, x, y, ep, big);
+                else csr_vector_rows<V, T, 2, 2>(base, M.m, M.rowptr, M.colidx, vals, x, y, ep, big);
+                break;
             case 4: csr_vector_rows<V, T, 4, 2>(base, M.m, M.rowptr, M.colidx, vals, x, y, ep, big); break;
             case 8: csr_vector_rows<V, T, 8, 2>(base, M.m, M.rowptr, M.colidx, vals, x, y, ep, big); break;
             case 16: csr_vector_rows<V, T, 16, 2>(base, M.m, M.rowptr, M.colidx, vals, x, y, ep, big); break;
@@ -259,14 +325,19 @@ int build(spmv_batch *b, cudaStream_t s) {
         M.m = h->m;
         M.nnz = h->nnz;
         M.mode = b->modes[i];
+        M.wide = wide_groups(h, M.mode);
         M.part_off = 0;
-        M.meta0 = nullptr;
+        M.meta0 = M.meta1 = nullptr;
         describe_format(h, M);
-        if (M.fmt == SPMV_FMT_CSR && M.mode == 0) {
+        if (M.mode == BATCH_COO && !M.coo_rows) M.mode = b->modes[i] = 0;  // COO chunks need COO rows
+        if (M.mode == BATCH_BSR) {
+            if (M.bsr_rowptr) M.fmt = SPMV_FMT_BSR;
+            else M.mode = b->modes[i] = default_mode(h);
+        }
+        if (M.fmt == SPMV_FMT_CSR && (M.mode == 0 || M.mode == BATCH_COO)) {
             const int64_t nch = (h->nnz + C - 1) / C;
-            SPMV_CUDA_TRY(dev_malloc((void **)&b->metas[i], sizeof(int32_t) * (nch + 1)));
-            SPMV_TRY(build_merge_meta(h->rowptr, h->m, h->nnz, C, b->metas[i], s));
-            M.meta0 = b->metas[i];
+            SPMV_TRY(build_chunk_meta(h, M.mode, C, &b->metas[i], s));
+            set_chunk_meta(M, b->metas[i], C);
             M.part_off = chunks_total;
             chunks_total += nch;
         }
@@ -370,9 +441,13 @@ int spmv_batch_create(spmv_batch_handle *out, const spmv_handle *hs, int32_t cou
     for (int i = 0; i < count; ++i) {
         BatchMat probe{};
         describe_format(hs[i], probe);
-        // ELL and SELL matrices run in their own format (mode -format); the
-        // others in a CSR mode
-        b->modes[i] = probe.fmt == SPMV_FMT_CSR ? default_mode(hs[i]) : -probe.fmt;
+        // ELL and SELL matrices run in their own format (mode -format), COO
+        // matrices as COO chunks (mode -2, which the tuner may trade for a
+        // CSR mode); the others in a CSR mode
+        b->modes[i] = probe.fmt != SPMV_FMT_CSR                 ? -probe.fmt
+                      : probe.coo_rows && hs[i]->nnz > 0   ? BATCH_COO
+                      : probe.bsr_rowptr && hs[i]->nnz > 0 ? BATCH_BSR
+                                                           : default_mode(hs[i]);
     }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -409,7 +484,7 @@ int spmv_batch_tune(spmv_batch_handle b, void *stream) {
         return SPMV_ERR_INVALID;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    const int cand[7] = {0, 1, 2, 4, 8, 16, 32};
+    const int cand[9] = {BATCH_COO, BATCH_BSR, 0, 1, 2, 4, 8, 16, 32};
     // 1) per matrix: time each mode on a one-matrix sub-batch
     for (int i = 0; i < b->count; ++i) {
         const spmv_matrix *h = b->hs[i];
@@ -417,12 +492,16 @@ int spmv_batch_tune(spmv_batch_handle b, void *stream) {
         {
             BatchMat probe{};
             describe_format(h, probe);
-            if (probe.fmt != SPMV_FMT_CSR) continue;  // ELL and SELL matrices run their own kernel bodies
+            if (probe.fmt != SPMV_FMT_CSR) continue;  // ELL and SELL matrices keep their own kernel bodies
         }
         int best_mode = b->modes[i];
         float best_t = 1e30f;
+        BatchMat probe{};
+        describe_format(h, probe);
         for (int mode : cand) {
-            if (mode == 0 && h->nnz == 0) continue;
+            if ((mode == 0 || mode == BATCH_COO) && h->nnz == 0) continue;
+            if (mode == BATCH_COO && !probe.coo_rows) continue;
+            if (mode == BATCH_BSR && (!probe.bsr_rowptr || h->nnz == 0)) continue;
             b->modes[i] = mode;
             spmv_batch one;  // a view of matrix i only (shares the counter, no graph)
             one.count = 1;
@@ -451,25 +530,43 @@ int spmv_batch_tune(spmv_batch_handle b, void *stream) {
             M.m = h->m;
             M.nnz = h->nnz;
             M.mode = mode;
-            M.fmt = SPMV_FMT_CSR;
-            int64_t off[2] = {0, mode == 0 ? (h->nnz + C - 1) / C : (h->m + 31) / 32};
+            M.wide = wide_groups(h, mode);
+            M.fmt = mode == BATCH_BSR ? SPMV_FMT_BSR : SPMV_FMT_CSR;
+            M.coo_rows = probe.coo_rows;
+            M.bsr_rowptr = probe.bsr_rowptr;
+            M.bsr_col = probe.bsr_col;
+            M.bsr_val = probe.bsr_val;
+            M.bsr_mb = probe.bsr_mb;
+            M.bsr_r = probe.bsr_r;
+            M.n = h->n;
+            // the mode is timed on k copies of the matrix in one launch (about
+            // 4M entries in all), so that a small matrix is timed at the
+            // throughput the full batch sees rather than at one launch's
+            // latency; the copies write the same y (timing only)
+            const int64_t per = batch_items(M, C);
+            const int64_t k = std::max<int64_t>(1, std::min<int64_t>(256, (int64_t(4) << 20) /
+                                                                              std::max<int64_t>(1, h->nnz + h->m)));
             int32_t *meta = nullptr;
             BatchMat *d_m = nullptr;
             int64_t *d_off = nullptr;
             int st = SPMV_OK;
-            if (mode == 0) {
-                if (dev_malloc((void **)&meta, sizeof(int32_t) * (off[1] + 1)) != cudaSuccess) st = SPMV_ERR_OOM;
-                if (st == SPMV_OK) st = build_merge_meta(h->rowptr, h->m, h->nnz, C, meta, s);
-                M.meta0 = meta;
-                if (st == SPMV_OK) st = alloc_partials(&one.part, off[1], 1, one.vt, s);
+            if (mode == 0 || mode == BATCH_COO) {
+                st = build_chunk_meta(h, mode, C, &meta, s);
+                if (st == SPMV_OK) set_chunk_meta(M, meta, C);
+                if (st == SPMV_OK) st = alloc_partials(&one.part, k * per, 1, one.vt, s);
             }
-            if (st == SPMV_OK && (dev_malloc((void **)&d_m, sizeof(BatchMat)) != cudaSuccess ||
-                                  dev_malloc((void **)&d_off, sizeof(off)) != cudaSuccess))
+            std::vector<BatchMat> copies((size_t)k, M);
+            std::vector<int64_t> offs((size_t)k + 1);
+            for (int64_t r = 0; r <= k; ++r) offs[r] = r * per;
+            for (int64_t r = 0; r < k; ++r) copies[r].part_off = mode == 0 || mode == BATCH_COO ? r * per : 0;
+            one.count = (int)k;
+            if (st == SPMV_OK && (dev_malloc((void **)&d_m, sizeof(BatchMat) * k) != cudaSuccess ||
+                                  dev_malloc((void **)&d_off, sizeof(int64_t) * (k + 1)) != cudaSuccess))
                 st = SPMV_ERR_OOM;
             if (st == SPMV_OK) {
-                cudaMemcpyAsync(d_m, &M, sizeof(M), cudaMemcpyHostToDevice, s);
-                cudaMemcpyAsync(d_off, off, sizeof(off), cudaMemcpyHostToDevice, s);
-                const float t = time_launch(&one, d_m, 1, d_off, off[1], s, 3, &st);
+                cudaMemcpyAsync(d_m, copies.data(), sizeof(BatchMat) * k, cudaMemcpyHostToDevice, s);
+                cudaMemcpyAsync(d_off, offs.data(), sizeof(int64_t) * (k + 1), cudaMemcpyHostToDevice, s);
+                const float t = time_launch(&one, d_m, (int)k, d_off, k * per, s, 3, &st);
                 if (st == SPMV_OK && t < best_t) {
                     best_t = t;
                     best_mode = mode;

@@ -1324,6 +1324,15 @@ int pack_sell(spmv_matrix *h, int kmax, bool grouped, cudaStream_t s) {
 }
 }  // namespace
 
+int build_coo_meta(const int32_t *rows, const int32_t *rowptr, int64_t nnz, int C, int32_t *meta0, int32_t *meta1,
+                   cudaStream_t s) {
+    const int64_t nchunks = (nnz + C - 1) / C;
+    if (nchunks == 0) return SPMV_OK;
+    k_seg_meta_coo<<<grid1d(nchunks + 1, 256), 256, 0, s>>>(rows, rowptr, nnz, C, nchunks, meta0, meta1);
+    SPMV_CUDA_TRY(cudaGetLastError());
+    return SPMV_OK;
+}
+
 int build_merge_meta(const int32_t *rowptr, int64_t m, int64_t nnz, int C, int32_t *meta, cudaStream_t s) {
     const int64_t nchunks = (nnz + C - 1) / C;
     k_seg_meta_merge<<<grid1d(nchunks + 1, 256), 256, 0, s>>>(rowptr, m, C, nchunks, meta);

@@ -367,6 +367,8 @@ int decode_ell_columns(const spmv_matrix *h, int32_t *d_out, cudaStream_t s);
 // chunk metadata kinds: COO / HYB tail, staged CSR tiles, CSR warp chunks
 enum { SEG_COO = 0, SEG_TILES = 1, SEG_MERGE = 2 };
 int ensure_seg_scratch(spmv_matrix *h, int items, int kind, cudaStream_t s);
+int build_coo_meta(const int32_t *rows, const int32_t *rowptr, int64_t nnz, int C, int32_t *meta0, int32_t *meta1,
+                   cudaStream_t s);
 int build_merge_meta(const int32_t *rowptr, int64_t m, int64_t nnz, int C, int32_t *meta, cudaStream_t s);
 int alloc_partials(Partials *p, int64_t units, int stride, int vt, cudaStream_t s);
 void free_partials(Partials *p);

@@ -391,49 +391,59 @@ template <> struct BlockRow<2, __nv_bfloat16, float> {
     }
 };
 
+// Block rows [base, base + 32 / (R S)) of a BSR matrix, R S lanes per block
+// row (S blocks at once, two steps in flight); block rows longer than
+// long_threshold blocks are left to k_bsr_long.  The whole warp calls it.
+template <typename V, typename T, int R, int S>
+__device__ __forceinline__ void bsr_rows(int64_t base, int64_t mb, int64_t m, int64_t n,
+                                         const int *__restrict__ browptr, const int *__restrict__ bcol,
+                                         const V *__restrict__ bval, const T *__restrict__ x, T *__restrict__ y,
+                                         const Epi<T> &ep, int long_threshold) {
+    constexpr int G = R * S;  // lanes per block row
+    const int lane = threadIdx.x & 31;
+    const int sub = lane % G, sblk = sub / R, i = sub % R;
+    const int64_t br = base + lane / G;
+    T acc = T(0);
+    bool skip = br >= mb;
+    if (!skip) {
+        const int bs = __ldg(browptr + br), be = __ldg(browptr + br + 1);
+        skip = be - bs > long_threshold;
+        // two blocks per step keep more loads in flight
+        for (int b = bs + sblk; !skip && b < be; b += 2 * S) {
+            const bool two = b + S < be;
+            const int64_t c0 = (int64_t)ld_s(bcol + b) * R;
+            const int64_t c1 = two ? (int64_t)ld_s(bcol + b + S) * R : c0;
+            T v0[R], v1[R];
+            BlockRow<R, V, T>::load(bval + (int64_t)b * R * R + i * R, v0);
+            if (two) BlockRow<R, V, T>::load(bval + (int64_t)(b + S) * R * R + i * R, v1);
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+                if (c0 + j < n) acc += v0[j] * ld_x(x, (int)(c0 + j));
+            if (two) {
+#pragma unroll
+                for (int j = 0; j < R; ++j)
+                    if (c1 + j < n) acc += v1[j] * ld_x(x, (int)(c1 + j));
+            }
+        }
+    }
+#pragma unroll
+    for (int off = G / 2; off >= R; off >>= 1) acc += __shfl_down_sync(FULLMASK, acc, off, G);
+    if (sblk == 0 && !skip) {
+        const int64_t row = br * R + i;
+        if (row < m) ep.store(y, row, acc);
+    }
+}
+
 template <typename V, typename T, int R, int S>
 __global__ void __launch_bounds__(1024)
 k_bsr(int64_t mb, int64_t m, int64_t n, const int *__restrict__ browptr, const int *__restrict__ bcol,
       const V *__restrict__ bval, const T *__restrict__ x, T *__restrict__ y, T alpha, T beta, int long_threshold) {
     const Epi<T> ep(alpha, beta);
-    constexpr int G = R * S;     // lanes per block row
-    constexpr int GPW = 32 / G;  // block rows per warp per step
-    const int lane = threadIdx.x & 31;
-    const int sub = lane % G, sblk = sub / R, i = sub % R;
+    constexpr int GPW = 32 / (R * S);  // block rows per warp per step
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t base = warp * GPW; base < mb; base += nwarps * GPW) {
-        const int64_t br = base + lane / G;
-        T acc = T(0);
-        bool skip = br >= mb;
-        if (!skip) {
-            const int bs = __ldg(browptr + br), be = __ldg(browptr + br + 1);
-            skip = be - bs > long_threshold;
-            // two blocks per step keep more loads in flight
-            for (int b = bs + sblk; !skip && b < be; b += 2 * S) {
-                const bool two = b + S < be;
-                const int64_t c0 = (int64_t)ld_s(bcol + b) * R;
-                const int64_t c1 = two ? (int64_t)ld_s(bcol + b + S) * R : c0;
-                T v0[R], v1[R];
-                BlockRow<R, V, T>::load(bval + (int64_t)b * R * R + i * R, v0);
-                if (two) BlockRow<R, V, T>::load(bval + (int64_t)(b + S) * R * R + i * R, v1);
-#pragma unroll
-                for (int j = 0; j < R; ++j)
-                    if (c0 + j < n) acc += v0[j] * ld_x(x, (int)(c0 + j));
-                if (two) {
-#pragma unroll
-                    for (int j = 0; j < R; ++j)
-                        if (c1 + j < n) acc += v1[j] * ld_x(x, (int)(c1 + j));
-                }
-            }
-        }
-#pragma unroll
-        for (int off = G / 2; off >= R; off >>= 1) acc += __shfl_down_sync(FULLMASK, acc, off, G);
-        if (sblk == 0 && !skip) {
-            const int64_t row = br * R + i;
-            if (row < m) ep.store(y, row, acc);
-        }
-    }
+    for (int64_t base = warp * GPW; base < mb; base += nwarps * GPW)
+        bsr_rows<V, T, R, S>(base, mb, m, n, browptr, bcol, bval, x, y, ep, long_threshold);
 }
 
 // Long BSR block rows: one thread block per segment of blocks; lane (g, i)

@@ -100,10 +100,82 @@ __device__ __forceinline__ T seg_carry(bool need, T fs, T pval) {
 // meta0[c] = first chunk of the row of entry c*C; meta1[c] = last chunk of
 // the row of the chunk's last entry.
 // ---------------------------------------------------------------------------
+// One COO chunk c (ACCUM: the COO part of HYB, adding into y); the whole
+// warp calls it.  WIDE: 32-byte loads (the handle's own arrays); the
+// allocation-free entry point runs on caller arrays aligned to 16 bytes only.
+template <typename V, typename T, int ITEMS, bool ACCUM, bool WIDE>
+__device__ __forceinline__ void coo_chunk(int64_t c, int64_t nnz, int64_t m, const int *__restrict__ rows,
+                                          const int *__restrict__ cols, const V *__restrict__ vals,
+                                          const T *__restrict__ x, T *__restrict__ y, const Epi<T> &ep,
+                                          const int *__restrict__ meta0, const int *__restrict__ meta1,
+                                          const PartialsT<T> &P) {
+    constexpr int C = 32 * ITEMS;
+    const int lane = threadIdx.x & 31;
+    const int64_t E0 = c * C, E1 = (E0 + C < nnz) ? E0 + C : nnz;
+    const int64_t a = E0 + (int64_t)lane * ITEMS;
+    const int cnt = E1 - a <= 0 ? 0 : (E1 - a >= ITEMS ? ITEMS : (int)(E1 - a));
+    const int last_lane = (int)((E1 - E0 - 1) / ITEMS);
+    int r[ITEMS];
+    T v[ITEMS], xv[ITEMS];
+    seg_load<V, T, ITEMS, true, WIDE>(E1 - E0 == C, a, cnt, rows, cols, vals, x, r, v, xv);
+
+    // row after this lane's range: next lane's first row, or the next
+    // chunk's first row (m past the last entry)
+    int nr = __shfl_down_sync(0xffffffffu, r[0], 1);
+    if (lane == last_lane) nr = E1 < nnz ? ld_s(rows + E1) : (int)m;
+    if (!ACCUM && c == 0 && lane == 0)
+        for (int q = 0; q < r[0]; ++q) seg_write<T, false>(y, q, T(0), ep);
+
+    int fr = r[0], cur = r[0];
+    T fs = T(0), acc = T(0);
+    bool fflush = false;
+    if (cnt > 0) {
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            if (j < cnt) {
+                if (r[j] != cur) {
+                    if (!fflush) { fs = acc; fflush = true; }
+                    else seg_write<T, ACCUM>(y, cur, acc, ep);
+                    if (!ACCUM)
+                        for (int q = cur + 1; q < r[j]; ++q) seg_write<T, false>(y, q, T(0), ep);
+                    cur = r[j];
+                    acc = T(0);
+                }
+                acc = fma(v[j], xv[j], acc);
+            }
+        }
+        if (nr != cur) {  // the last row ends exactly at the lane's end
+            if (!fflush) { fs = acc; fflush = true; }
+            else seg_write<T, ACCUM>(y, cur, acc, ep);
+            if (!ACCUM)
+                for (int q = cur + 1; q < nr; ++q) seg_write<T, false>(y, q, T(0), ep);
+            cur = nr;
+            acc = T(0);
+        }
+    }
+    const int key = cnt > 0 ? cur : -1;
+    const T sc = seg_scan<T>(key, cnt > 0 ? acc : T(0));
+    const int pkey = __shfl_up_sync(0xffffffffu, key, 1);
+    const T pval = __shfl_up_sync(0xffffffffu, sc, 1);
+    const int H = __shfl_sync(0xffffffffu, r[0], 0);
+    const int64_t hc0 = meta0[c], tc1 = meta1[c];
+    const bool h_back = hc0 < c, t_fwd = tc1 > c;
+    const T total = seg_carry<T>(cnt > 0 && fflush && lane > 0 && pkey == fr, fs, pval);
+    if (cnt > 0 && fflush) {
+        if (fr == H && h_back)  // H started in an earlier chunk and ends in this one
+            seg_arrive<T, ACCUM>(fr, c, hc0, c, total, P, y, ep);
+        else
+            seg_write<T, ACCUM>(y, fr, total, ep);
+    }
+    if (lane == last_lane && t_fwd) {
+        // the open row at the chunk end (cur == nr) continues into the next chunk
+        const int64_t c0 = (cur == H && h_back) ? hc0 : c;
+        seg_arrive<T, ACCUM>(cur, c, c0, tc1, sc, P, y, ep);
+    }
+}
+
 // 16 items per lane need more than 64 registers: those variants are limited
 // to 512-thread blocks.
-// WIDE: 32-byte loads (the handle's own arrays); the allocation-free entry
-// point runs on caller arrays aligned to 16 bytes only
 template <typename V, typename T, int ITEMS, bool ACCUM, bool WIDE = false>
 __global__ void __launch_bounds__(ITEMS >= 16 ? 512 : 1024) __maxnreg__(ITEMS >= 16 ? 128 : 64)
 k_coo_seg(int64_t nnz, int64_t m, const int *__restrict__ rows, const int *__restrict__ cols,
@@ -111,73 +183,11 @@ k_coo_seg(int64_t nnz, int64_t m, const int *__restrict__ rows, const int *__res
           const int *__restrict__ meta0, const int *__restrict__ meta1, const PartialsT<T> P) {
     const Epi<T> ep(alpha, beta);
     constexpr int C = 32 * ITEMS;
-    const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t nchunks = (nnz + C - 1) / C;
-    for (int64_t c = warp; c < nchunks; c += nwarps) {
-        const int64_t E0 = c * C, E1 = (E0 + C < nnz) ? E0 + C : nnz;
-        const int64_t a = E0 + (int64_t)lane * ITEMS;
-        const int cnt = E1 - a <= 0 ? 0 : (E1 - a >= ITEMS ? ITEMS : (int)(E1 - a));
-        const int last_lane = (int)((E1 - E0 - 1) / ITEMS);
-        int r[ITEMS];
-        T v[ITEMS], xv[ITEMS];
-        seg_load<V, T, ITEMS, true, WIDE>(E1 - E0 == C, a, cnt, rows, cols, vals, x, r, v, xv);
-
-        // row after this lane's range: next lane's first row, or the next
-        // chunk's first row (m past the last entry)
-        int nr = __shfl_down_sync(0xffffffffu, r[0], 1);
-        if (lane == last_lane) nr = E1 < nnz ? ld_s(rows + E1) : (int)m;
-        if (!ACCUM && c == 0 && lane == 0)
-            for (int q = 0; q < r[0]; ++q) seg_write<T, false>(y, q, T(0), ep);
-
-        int fr = r[0], cur = r[0];
-        T fs = T(0), acc = T(0);
-        bool fflush = false;
-        if (cnt > 0) {
-#pragma unroll
-            for (int j = 0; j < ITEMS; ++j) {
-                if (j < cnt) {
-                    if (r[j] != cur) {
-                        if (!fflush) { fs = acc; fflush = true; }
-                        else seg_write<T, ACCUM>(y, cur, acc, ep);
-                        if (!ACCUM)
-                            for (int q = cur + 1; q < r[j]; ++q) seg_write<T, false>(y, q, T(0), ep);
-                        cur = r[j];
-                        acc = T(0);
-                    }
-                    acc = fma(v[j], xv[j], acc);
-                }
-            }
-            if (nr != cur) {  // the last row ends exactly at the lane's end
-                if (!fflush) { fs = acc; fflush = true; }
-                else seg_write<T, ACCUM>(y, cur, acc, ep);
-                if (!ACCUM)
-                    for (int q = cur + 1; q < nr; ++q) seg_write<T, false>(y, q, T(0), ep);
-                cur = nr;
-                acc = T(0);
-            }
-        }
-        const int key = cnt > 0 ? cur : -1;
-        const T sc = seg_scan<T>(key, cnt > 0 ? acc : T(0));
-        const int pkey = __shfl_up_sync(0xffffffffu, key, 1);
-        const T pval = __shfl_up_sync(0xffffffffu, sc, 1);
-        const int H = __shfl_sync(0xffffffffu, r[0], 0);
-        const int64_t hc0 = meta0[c], tc1 = meta1[c];
-        const bool h_back = hc0 < c, t_fwd = tc1 > c;
-        const T total = seg_carry<T>(cnt > 0 && fflush && lane > 0 && pkey == fr, fs, pval);
-        if (cnt > 0 && fflush) {
-            if (fr == H && h_back)  // H started in an earlier chunk and ends in this one
-                seg_arrive<T, ACCUM>(fr, c, hc0, c, total, P, y, ep);
-            else
-                seg_write<T, ACCUM>(y, fr, total, ep);
-        }
-        if (lane == last_lane && t_fwd) {
-            // the open row at the chunk end (cur == nr) continues into the next chunk
-            const int64_t c0 = (cur == H && h_back) ? hc0 : c;
-            seg_arrive<T, ACCUM>(cur, c, c0, tc1, sc, P, y, ep);
-        }
-    }
+    for (int64_t c = warp; c < nchunks; c += nwarps)
+        coo_chunk<V, T, ITEMS, ACCUM, WIDE>(c, nnz, m, rows, cols, vals, x, y, ep, meta0, meta1, P);
 }
 
 // ---------------------------------------------------------------------------

@@ -189,8 +189,9 @@ FORMAT_CYCLE = [B.FMT_ELL, B.FMT_SELL, B.FMT_CSR, B.FMT_COO, B.FMT_HYB, B.FMT_BS
 @pytest.mark.parametrize("vt", [B.SPMV_F32, B.SPMV_F64, B.SPMV_BF16])
 def test_batch_runs_each_matrix_in_its_format(oracle, vt):
     """Handles in ELL and SELL run in their own format inside the batch
-    (modes -1 and -5), the others from their CSR arrays; every product
-    matches the oracle before and after the autotuner."""
+    (modes -1 and -5), COO and BSR handles as COO chunks and BSR block rows
+    (modes -2, -4) until the tuner picks, the others from their CSR arrays;
+    every product matches the oracle before and after the autotuner."""
     import torch
     mats = batch_matrices(count=36, seed=3)
     hs, xs, ys, xh = [], [], [], []
@@ -203,7 +204,8 @@ def test_batch_runs_each_matrix_in_its_format(oracle, vt):
         except B.SpmvError:
             fmt = B.FMT_CSR                      # a padded format over its limit: the handle stays CSR
         hs.append(h)
-        want_modes.append(-fmt if fmt in (B.FMT_ELL, B.FMT_SELL) else None)
+        want_modes.append(-fmt if fmt in (B.FMT_ELL, B.FMT_SELL) or (fmt in (B.FMT_COO, B.FMT_BSR) and coo.nnz > 0)
+                          else None)
         x = matgen.dense_vector(coo.n, 70 + i)
         xh.append(x)
         xs.append(torch.from_numpy(x).to(vec_dtype(vt)).cuda())
@@ -220,6 +222,12 @@ def test_batch_runs_each_matrix_in_its_format(oracle, vt):
         for tuned in (False, True):
             if tuned:
                 B.spmv_batch_tune(b)
+                modes, _, _ = B.spmv_batch_get_plan(b, len(mats))
+                for i, wm in enumerate(want_modes):   # the tuner keeps ELL and SELL, may move COO, BSR to CSR
+                    if wm in (-B.FMT_COO, -B.FMT_BSR):
+                        assert modes[i] == wm or modes[i] >= 0, i
+                    elif wm is not None and mats[i].m > 0:
+                        assert modes[i] == wm, i
             for y in ys:
                 y.fill_(float("nan"))
             B.spmv_batch_launch(b)
