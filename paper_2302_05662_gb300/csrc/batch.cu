@@ -20,6 +20,7 @@
 
 struct spmv_batch {
     int count = 0, vt = SPMV_F64, items = 8, tpb = 256, sm_count = 0;
+    int group = 4;  // work units (chunks, row groups, SELL items) per batch item
     std::vector<spmv_handle> hs;
     std::vector<double> alpha, beta;
     std::vector<const void *> x;
@@ -49,6 +50,7 @@ struct BatchMat {
     double alpha, beta;
     int64_t m, nnz;
     int64_t part_off;  // first chunk of this matrix in the batch partials
+    int64_t units;     // work units of this matrix (batch items take `group` of them)
     const int *meta0;  // split: first row starting at or after each chunk's first entry;
                        // COO: first chunk of each chunk's head row
     const int *meta1;  // COO: last chunk of each chunk's tail row
@@ -160,7 +162,7 @@ int wide_groups(const spmv_matrix *h, int mode) {
 template <typename V, typename T, int ITEMS>
 __global__ void __launch_bounds__(512) __maxnreg__(ITEMS >= 16 ? 128 : (sizeof(T) == 8 ? 96 : 64))
 k_batch(const BatchMat *__restrict__ mats, int count, const int64_t *__restrict__ item_off, int64_t total,
-        unsigned long long *counter, const PartialsT<T> P) {
+        int group, unsigned long long *counter, const PartialsT<T> P) {
     __shared__ MergeSmem<ITEMS> s_merge[16];  // split chunks: one per warp
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -174,11 +176,13 @@ k_batch(const BatchMat *__restrict__ mats, int count, const int64_t *__restrict_
             if ((unsigned long long)__ldg(item_off + mid) <= item) lo = mid; else hi = mid - 1;
         }
         const BatchMat &M = mats[lo];  // fields read where a branch needs them
-        const int64_t local = (int64_t)item - __ldg(item_off + lo);
+        const int64_t u0 = ((int64_t)item - __ldg(item_off + lo)) * group;
+        const int64_t u1 = u0 + group < M.units ? u0 + group : M.units;
         const Epi<T> ep((T)M.alpha, (T)M.beta);
         const V *vals = (const V *)M.vals;
         const T *x = (const T *)M.x;
         T *y = (T *)M.y;
+        for (int64_t local = u0; local < u1; ++local) {
         if (M.fmt == SPMV_FMT_ELL) {  // 32 rows, one per lane
             const int64_t r = local * 32 + lane;
             if (r < M.m) {
@@ -239,6 +243,7 @@ k_batch(const BatchMat *__restrict__ mats, int count, const int64_t *__restrict_
             default: csr_vector_rows<V, T, 32, 2>(base, M.m, M.rowptr, M.colidx, vals, x, y, ep, big); break;
             }
         }
+        }
     }
 }
 
@@ -250,7 +255,7 @@ int launch_batch_t(const spmv_batch *b, const BatchMat *mats, int count, const i
     const int64_t need = (total + b->tpb / 32 - 1) / (b->tpb / 32);
     const int64_t cap = (int64_t)per_sm * b->sm_count;
     const int grid = (int)std::max<int64_t>(1, std::min(need, cap));
-    kern<<<grid, b->tpb, 0, s>>>(mats, count, item_off, total, b->d_counter, PartialsT<T>::of(b->part));
+    kern<<<grid, b->tpb, 0, s>>>(mats, count, item_off, total, b->group, b->d_counter, PartialsT<T>::of(b->part));
     SPMV_CUDA_TRY(cudaGetLastError());
     return SPMV_OK;
 }
@@ -341,7 +346,8 @@ int build(spmv_batch *b, cudaStream_t s) {
             M.part_off = chunks_total;
             chunks_total += nch;
         }
-        off[i + 1] = off[i] + batch_items(M, C);
+        M.units = batch_items(M, C);
+        off[i + 1] = off[i] + (M.units + b->group - 1) / b->group;
     }
     b->total_items = off[b->count];
     SPMV_TRY(alloc_partials(&b->part, chunks_total, 1, b->vt, s));
@@ -508,6 +514,7 @@ int spmv_batch_tune(spmv_batch_handle b, void *stream) {
             one.vt = b->vt;
             one.items = b->items;
             one.tpb = b->tpb;
+            one.group = 1;
             one.sm_count = b->sm_count;
             one.hs = {b->hs[i]};
             one.alpha = {b->alpha[i]};
@@ -555,6 +562,7 @@ int spmv_batch_tune(spmv_batch_handle b, void *stream) {
                 if (st == SPMV_OK) set_chunk_meta(M, meta, C);
                 if (st == SPMV_OK) st = alloc_partials(&one.part, k * per, 1, one.vt, s);
             }
+            M.units = per;
             std::vector<BatchMat> copies((size_t)k, M);
             std::vector<int64_t> offs((size_t)k + 1);
             for (int64_t r = 0; r <= k; ++r) offs[r] = r * per;
@@ -583,26 +591,31 @@ int spmv_batch_tune(spmv_batch_handle b, void *stream) {
         b->modes[i] = best_mode;
     }
     // 2) batch-wide: chunk size and block size on the whole batch
-    int best_items = b->items, best_tpb = b->tpb;
+    int best_items = b->items, best_tpb = b->tpb, best_group = b->group;
     float best_t = 1e30f;
-    for (int items : {4, 8, 16}) {
-        for (int tpb : {128, 256, 512}) {
-            b->items = items;
-            b->tpb = tpb;
-            SPMV_TRY(build(b, s));
-            int st = SPMV_OK;
-            const float t = time_launch(b, (const BatchMat *)b->d_mats, b->count, b->d_item_off, b->total_items, s,
-                                        5, &st);
-            SPMV_TRY(st);
-            if (t < best_t) {
-                best_t = t;
-                best_items = items;
-                best_tpb = tpb;
+    for (int group : {1, 4}) {
+        for (int items : {4, 8, 16}) {
+            for (int tpb : {128, 256, 512}) {
+                b->items = items;
+                b->tpb = tpb;
+                b->group = group;
+                SPMV_TRY(build(b, s));
+                int st = SPMV_OK;
+                const float t = time_launch(b, (const BatchMat *)b->d_mats, b->count, b->d_item_off,
+                                            b->total_items, s, 5, &st);
+                SPMV_TRY(st);
+                if (t < best_t) {
+                    best_t = t;
+                    best_items = items;
+                    best_tpb = tpb;
+                    best_group = group;
+                }
             }
         }
     }
     b->items = best_items;
     b->tpb = best_tpb;
+    b->group = best_group;
     return build(b, s);
 }
 
