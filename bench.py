@@ -77,7 +77,10 @@ def parse():
                         "by nnz-balanced row blocks with an all-gather of x (strong scaling)")
     p.add_argument("--fixed", default=None,
                    help="profiling runs: skip tuning and selection, run this kernel variant's default "
-                        "configuration (csr, csr_split, ell, coo, hyb, bsr)")
+                        "configuration (csr, csr_split, csr_tiles, ell, coo, hyb, bsr, sell)")
+    p.add_argument("--config", default=None,
+                   help="profiling runs: like --fixed, with these spmv_config fields (a JSON object, "
+                        "e.g. '{\"format\": 0, \"threads_per_row\": 2}')")
     return p.parse_args()
 
 
@@ -612,9 +615,9 @@ def ours(args, world, rank, local):
         B.spmv_features(h)
         t_feat = time.perf_counter() - t0
         nbytes = byte_model(coo.m, coo.n, nnz, vsz, xsz)
-        if args.fixed:
+        if args.fixed or args.config:
             from paper_2302_05662_gb300.workload import SWEEP_VARIANTS
-            fixed = dict(dict(SWEEP_VARIANTS)[args.fixed])
+            fixed = json.loads(args.config) if args.config else dict(dict(SWEEP_VARIANTS)[args.fixed])
             B.spmv_set_config(h, B.make_config(**fixed))
             t = timer.time_us(h, x, y, reps=3)
             best_cfg, best_t, per_fmt = fixed, t, {fmt_name(fixed): (fixed, t)}
@@ -628,9 +631,9 @@ def ours(args, world, rank, local):
             format_sweep.append({"matrix": mname, "kernel": fname, "config": cfg, "us": round(t, 2),
                                  "gflops": round(2 * nnz / (t * 1e-6) / 1e9, 1), "gbs": round(gbs, 1),
                                  "format_gbs": round(fb / (t * 1e-6) / 1e9, 1)})
-        chosen, source = best_cfg, ("fixed" if args.fixed else "exhaustive")
+        chosen, source = best_cfg, ("fixed" if args.fixed or args.config else "exhaustive")
         t_sel = t_pack = None
-        if have_selector and not args.fixed:
+        if have_selector and not (args.fixed or args.config):
             B.spmv_set_config(h, B.make_config(format=B.FMT_CSR))
             gate = None
             if have_v2:
@@ -845,12 +848,13 @@ def ours(args, world, rank, local):
         fs["format_frac"] = round(fs["format_gbs"] / peak, 4)
     clocks = clk.summary()
     batched = cg = None
-    if not args.no_batched and only is None and not args.fixed:
+    if not args.no_batched and only is None and not (args.fixed or args.config):
         batched = batched_section(B, matgen, torch)
     energy_rep = None
-    if not args.no_energy and not args.fixed:
+    if not args.no_energy and not (args.fixed or args.config):
         energy_rep = energy_section(B, torch, mats, gpu_index)
-    if not args.no_cg and only is None and not args.fixed and args.scale == "full" and vt == B.SPMV_F64:
+    profiling = bool(args.fixed or args.config)
+    if not args.no_cg and only is None and not profiling and args.scale == "full" and vt == B.SPMV_F64:
         cg = cg_section(B, matgen, torch, S, have_v2)
     if rank != 0:
         for p in mats:

@@ -359,6 +359,18 @@ SPMV_API int spmv_features(spmv_handle h, double *h_out, void *stream);
 SPMV_API int spmv_selector_load(const float *h_blob, int64_t count);
 
 /*
+ * Load a selector for handles of one value type only (SPMV_F64, SPMV_F32,
+ * SPMV_BF16), in the blob format above: spmv_select and spmv_select_runtime
+ * on a handle of that type use it, and the one spmv_selector_load loaded
+ * for the other types (labels measured on one value type need not carry to
+ * another: on GB300 fp64 products are bound by the fp64 pipe as much as by
+ * HBM).  A NULL blob with count 0 unloads it.  spmv_selector_infer uses the
+ * shared selector only.  Errors: SPMV_ERR_INVALID for an unknown value type
+ * or a malformed blob.
+ */
+SPMV_API int spmv_selector_load_vt(int32_t value_type, const float *h_blob, int64_t count);
+
+/*
  * Run the selector's fused inference kernel on host features (20 doubles):
  * writes the chosen class to *choice and, when h_logits is not NULL, the K
  * output logits (fp32).  Synchronises `stream`.  SPMV_ERR_INVALID if no

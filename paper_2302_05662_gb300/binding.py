@@ -29,7 +29,7 @@ TPR_SPLIT = -1
 # every entry point include/spmv.h declares (checked by the CPU test suite)
 EXPORTED = ("spmv_config_default", "spmv_create", "spmv_set_config", "spmv_get_config",
             "spmv_get_info", "spmv_run", "spmv_export_bytes", "spmv_export", "spmv_destroy",
-            "spmv_last_error", "spmv_coo_run_noalloc", "spmv_features", "spmv_selector_load",
+            "spmv_last_error", "spmv_coo_run_noalloc", "spmv_features", "spmv_selector_load", "spmv_selector_load_vt",
             "spmv_selector_infer", "spmv_select", "spmv_batch_create", "spmv_batch_tune",
             "spmv_batch_launch", "spmv_batch_get_plan", "spmv_batch_destroy", "spmv_batch_run",
             "spmv_select_runtime", "spmv_cg", "spmv_set_panel_limit", "spmv_get_panel_limit",
@@ -121,6 +121,7 @@ def load_library(path: str | None = None):
         "spmv_batch_run": (ctypes.c_int, [_VP, _I32, _VP, _VP, _VP, _VP, _VP]),
         "spmv_features": (ctypes.c_int, [_VP, _VP, _VP]),
         "spmv_selector_load": (ctypes.c_int, [_VP, _I64]),
+        "spmv_selector_load_vt": (ctypes.c_int, [ctypes.c_int32, _VP, _I64]),
         "spmv_selector_infer": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(_I32), _VP]),
         "spmv_select": (ctypes.c_int, [_VP, ctypes.POINTER(spmv_config), _VP, _VP]),
         "spmv_select_runtime": (ctypes.c_int, [_VP, _I64, ctypes.POINTER(spmv_config),
@@ -307,6 +308,17 @@ def spmv_selector_load(blob):
 def spmv_selector_unload():
     """Unload the selector on the current device (spmv_selector_load(NULL, 0))."""
     _check(load_library().spmv_selector_load(None, 0))
+
+
+def spmv_selector_load_vt(value_type: int, blob=None):
+    """Load (or, with blob None, unload) the selector used for handles of
+    one value type on the current device."""
+    import numpy as np
+    if blob is None:
+        _check(load_library().spmv_selector_load_vt(int(value_type), None, 0))
+        return
+    b = np.ascontiguousarray(blob, dtype=np.float32)
+    _check(load_library().spmv_selector_load_vt(int(value_type), b.ctypes.data, int(b.size)))
 
 
 def spmv_selector_infer(features, k: int, stream=None):

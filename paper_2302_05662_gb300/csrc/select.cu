@@ -41,7 +41,9 @@ struct Selector {
 };
 
 std::mutex g_sel_mu;
-Selector g_sel[64];
+// per device: slot 0 the selector for every value type, slots 1..3 one for
+// fp64 / fp32 / bf16 values that takes precedence when loaded
+Selector g_sel[64][4];
 
 __global__ void __launch_bounds__(256)
 k_mlp(const double *feat, const float *w, int F, int H, int K, int time_head, int *choice, float *logits,
@@ -86,11 +88,18 @@ k_mlp(const double *feat, const float *w, int F, int H, int K, int time_head, in
     }
 }
 
-Selector *current_selector(int *dev_out) {
+Selector *current_selector(int *dev_out, int slot = 0) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
     if (dev_out) *dev_out = dev;
-    return &g_sel[dev];
+    return &g_sel[dev][slot];
+}
+
+// the selector a handle uses: its value type's if loaded, else the shared one
+Selector *selector_for(const spmv_matrix *h) {
+    Selector *own = current_selector(nullptr, 1 + h->vt);
+    if (own && own->K > 0) return own;
+    return current_selector(nullptr, 0);
 }
 
 void default_csr_config(spmv_config *c) { spmv_config_default(c, SPMV_FMT_CSR); }
@@ -172,10 +181,10 @@ int spmv_features(spmv_handle h, double *h_out, void *stream) {
     return st;
 }
 
-int spmv_selector_load(const float *h_blob, int64_t count) {
-    entry_reset();
+namespace {
+int selector_load_slot(int slot, const float *h_blob, int64_t count) {
     if (!h_blob && count == 0) {  // unload: spmv_select falls back to default CSR
-        Selector *sel = current_selector(nullptr);
+        Selector *sel = current_selector(nullptr, slot);
         if (!sel) {
             set_error("spmv_selector_load: no current device");
             return SPMV_ERR_CUDA;
@@ -213,7 +222,7 @@ int spmv_selector_load(const float *h_blob, int64_t count) {
             return SPMV_ERR_INVALID;
         }
     int dev = 0;
-    Selector *sel = current_selector(&dev);
+    Selector *sel = current_selector(&dev, slot);
     if (!sel) {
         set_error("spmv_selector_load: no current device");
         return SPMV_ERR_CUDA;
@@ -246,6 +255,21 @@ int spmv_selector_load(const float *h_blob, int64_t count) {
     sel->K = K;
     sel->version = version;
     return SPMV_OK;
+}
+}  // namespace
+
+int spmv_selector_load(const float *h_blob, int64_t count) {
+    entry_reset();
+    return selector_load_slot(0, h_blob, count);
+}
+
+int spmv_selector_load_vt(int32_t value_type, const float *h_blob, int64_t count) {
+    entry_reset();
+    if (value_type != SPMV_F64 && value_type != SPMV_F32 && value_type != SPMV_BF16) {
+        set_error("spmv_selector_load_vt: unknown value type %d", value_type);
+        return SPMV_ERR_INVALID;
+    }
+    return selector_load_slot(1 + value_type, h_blob, count);
 }
 
 int spmv_selector_infer(const double *h_features, float *h_logits, int32_t *choice, void *stream) {
@@ -285,7 +309,7 @@ int spmv_select(spmv_handle h, spmv_config *out_cfg, double *h_features, void *s
         set_error("spmv_select: NULL argument");
         return SPMV_ERR_INVALID;
     }
-    Selector *sel = current_selector(nullptr);
+    Selector *sel = selector_for(h);
     double hf[SPMV_NUM_FEATURES];
     int choice = -1;
     SPMV_TRY(run_selector(h, sel, (cudaStream_t)stream, hf, &choice, nullptr));
@@ -302,7 +326,7 @@ int spmv_select_runtime(spmv_handle h, int64_t expected_runs, spmv_config *out_c
         set_error("spmv_select_runtime: bad argument");
         return SPMV_ERR_INVALID;
     }
-    Selector *sel = current_selector(nullptr);
+    Selector *sel = selector_for(h);
     if (!sel || sel->K == 0 || sel->version < 2) {
         set_error("spmv_select_runtime: needs a loaded selector with a time head (blob version 2)");
         return SPMV_ERR_INVALID;

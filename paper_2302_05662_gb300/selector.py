@@ -25,6 +25,8 @@ from . import binding as B
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_BLOB = os.path.join(PKG, "selector_gb300.f32")
+# trained on fp32-value sweeps; used for fp32 and bf16 handles when present
+LOWP_BLOB = os.path.join(PKG, "selector_gb300_fp32_values.f32")
 # the exhaustive-sweep records the committed selector was trained on: the
 # full sweep, a supplementary SELL sweep of the same 2000 matrices, and the
 # conversion-time calibration of its cost model
@@ -95,10 +97,17 @@ def parse_blob(blob) -> dict:
     return out
 
 
-def load_default_selector(path: str = DEFAULT_BLOB) -> dict:
-    """Load the committed trained selector onto the current device."""
+def load_default_selector(path: str = DEFAULT_BLOB, lowp_path: str | None = LOWP_BLOB) -> dict:
+    """Load the committed trained selector onto the current device (for every
+    value type), and the one trained on fp32 values, if present, for fp32
+    and bf16 handles."""
     blob = np.fromfile(path, dtype=np.float32)
     B.spmv_selector_load(blob)
+    for vt in (B.SPMV_F32, B.SPMV_BF16):
+        if lowp_path and os.path.exists(lowp_path):
+            B.spmv_selector_load_vt(vt, np.fromfile(lowp_path, dtype=np.float32))
+        else:
+            B.spmv_selector_load_vt(vt, None)
     return parse_blob(blob)
 
 

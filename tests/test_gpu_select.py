@@ -123,6 +123,40 @@ def test_select_returns_label_and_falls_back():
         B.spmv_selector_unload()
 
 
+def _fixed_choice_blob(k, label, seed=2):
+    w, labels = _random_selector(seed=seed)
+    w["W2"][:] = 0.0
+    w["b2"][:] = 0.0
+    w["b2"][k] = 1.0
+    labels[k] = label
+    return S.make_blob(w["mu"], w["sigma"], w["W1"], w["b1"], w["W2"], w["b2"], labels)
+
+
+def test_value_type_selector_takes_precedence():
+    """A selector loaded for one value type answers for handles of that type;
+    the shared selector still answers for the others, and again once the
+    per-type one is unloaded."""
+    coo = CASES[0][1]
+    h64, h32 = create(coo, B.SPMV_F64), create(coo, B.SPMV_F32)
+    try:
+        B.spmv_selector_load(_fixed_choice_blob(5, dict(format=B.FMT_HYB, threads_per_block=128)))
+        B.spmv_selector_load_vt(B.SPMV_F32, _fixed_choice_blob(7, dict(format=B.FMT_SELL, threads_per_block=64)))
+        c64, _ = B.spmv_select(h64)
+        c32, _ = B.spmv_select(h32)
+        assert (c64.format, c64.threads_per_block) == (B.FMT_HYB, 128)
+        assert (c32.format, c32.threads_per_block) == (B.FMT_SELL, 64)
+        B.spmv_selector_load_vt(B.SPMV_F32, None)
+        c32, _ = B.spmv_select(h32)
+        assert (c32.format, c32.threads_per_block) == (B.FMT_HYB, 128)
+        with pytest.raises(B.SpmvError):
+            B.spmv_selector_load_vt(7, _fixed_choice_blob(1, dict(format=B.FMT_ELL)))
+    finally:
+        B.spmv_destroy(h64)
+        B.spmv_destroy(h32)
+        B.spmv_selector_load_vt(B.SPMV_F32, None)
+        B.spmv_selector_unload()
+
+
 def test_bad_blob_rejected():
     w, labels = _random_selector()
     blob = S.make_blob(w["mu"], w["sigma"], w["W1"], w["b1"], w["W2"], w["b2"], labels)
