@@ -390,6 +390,39 @@ def evaluate_refined(choice_keys, ids, refine: dict, T, labels_keys, table: dict
     return {"with_knob_table": summ(slow_k), "class_only": summ(slow_0)}
 
 
+def evaluate_retimed(paths) -> dict:
+    """The held-out judge measured on the GPU (sweep --heldout-eval): per
+    matrix, the device selector's pick and the refined exhaustive best
+    (label space, then register cap x unroll x carveout around its winner)
+    timed again in one session with interleaved repetitions.  Slowdown =
+    t(pick) / t(refined best); also with the per-class knob table applied to
+    the pick, and the pick's speedup over default CSR."""
+    import gzip
+    recs = []
+    for path in paths:
+        with (gzip.open(path, "rt") if path.endswith(".gz") else open(path)) as fh:
+            recs += [json.loads(l) for l in fh if l.strip()]
+    def summ(rs):
+        slow = np.array([r["final"]["pick"] / r["final"]["winner"] for r in rs])
+        slk = np.array([r["final"].get("pick_knob_table", r["final"]["pick"]) / r["final"]["winner"] for r in rs])
+        spd = np.array([r["final"]["default_csr"] / r["final"]["pick"] for r in rs])
+        best = np.array([r["final"]["default_csr"] / r["final"]["winner"] for r in rs])
+        return {"n": len(rs), "within_10pct": float(np.mean(slow <= 1.10)),
+                "median_slowdown": float(np.median(slow)), "max_slowdown": float(slow.max()),
+                "geomean_slowdown": float(np.exp(np.mean(np.log(slow)))),
+                "within_10pct_with_knob_table": float(np.mean(slk <= 1.10)),
+                "geomean_slowdown_with_knob_table": float(np.exp(np.mean(np.log(slk)))),
+                "geomean_speedup_vs_default_csr": float(np.exp(np.mean(np.log(spd)))),
+                "geomean_best_vs_default_csr": float(np.exp(np.mean(np.log(best))))}
+    out = {"all": summ(recs), "dtype": sorted({r["dtype"] for r in recs}),
+           "flush": sorted({r["flush"] for r in recs})}
+    out["by_family"] = {f: summ([r for r in recs if r["family"] == f]) for f in sorted({r["family"] for r in recs})}
+    sizes = (("under_15us", 0, 15), ("15_to_40us", 15, 40), ("over_40us", 40, float("inf")))
+    out["by_refined_best_time"] = {k: summ([r for r in recs if lo <= r["final"]["winner"] < hi])
+                                   for k, lo, hi in sizes if any(lo <= r["final"]["winner"] < hi for r in recs)}
+    return out
+
+
 def main():
     """Train on the sweep records (matrices 0-1799), evaluate on 1800-1999,
     write the blob and a JSON report.  With --calib (conversion-time
@@ -409,6 +442,9 @@ def main():
     ap.add_argument("--refine", nargs="*", default=None,
                     help="refine records (sweep --refine-from): evaluate a per-class register cap / unroll / "
                          "carveout table against the refined exhaustive best")
+    ap.add_argument("--heldout-retimed", nargs="*", default=None,
+                    help="records of sweep --heldout-eval: the GPU-measured judge of the blob, added to "
+                         "the report")
     ap.add_argument("--apply-knobs", action="store_true",
                     help="write the per-class knob table into the blob's labels (default: report only)")
     args = ap.parse_args()
@@ -500,6 +536,8 @@ def main():
             choice = np.argmax(logits, axis=1)
             report[name + "_vs_refined_best"] = evaluate_refined([keys[c] for c in choice], ids[msk], refine,
                                                                  T[msk], keys, table)
+    if args.heldout_retimed:
+        report["heldout_retimed"] = evaluate_retimed(args.heldout_retimed)
     blob = make_blob(w["mu"], w["sigma"], w["W1"], w["b1"], w["W2"], w["b2"], labels, W3, b3, pack)
     blob.tofile(args.out)
     txt = json.dumps(report, indent=1)
