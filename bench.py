@@ -591,7 +591,7 @@ def ours(args, world, rank, local):
         if rank == 0:
             print(json.dumps({"batched": batched_section(B, matgen, torch, count=args.batched_only)}), flush=True)
         return
-    timer = sweep.Timer()
+    timer = sweep.Timer(flush="read", stat="trimmed")
 
     only = set(args.only.split(",")) if args.only else None
     mats = []          # per matrix: name, handle, x, y, nnz, bytes, chosen cfg

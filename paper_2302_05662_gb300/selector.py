@@ -27,12 +27,15 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_BLOB = os.path.join(PKG, "selector_gb300.f32")
 # trained on fp32-value sweeps; used for fp32 and bf16 handles when present
 LOWP_BLOB = os.path.join(PKG, "selector_gb300_fp32_values.f32")
-# the exhaustive-sweep records the committed selector was trained on: the
-# full sweep, a supplementary SELL sweep of the same 2000 matrices, and the
-# conversion-time calibration of its cost model
-DEFAULT_DATA = os.path.join(PKG, "data", "sweep_gb300_f64.jsonl.gz")
-DEFAULT_SUPPLEMENT = os.path.join(PKG, "data", "sweep_gb300_f64_sell.jsonl.gz")
+# the exhaustive-sweep records the committed fp64 selector was trained on
+# (every label point of the 2000 dataset matrices, L2 flushed by reading,
+# trimmed means), the conversion-time calibration of its cost model, and the
+# GPU-measured held-out judges (sweep --heldout-eval) of the fp64 and fp32
+# selectors
+DEFAULT_DATA = os.path.join(PKG, "data", "sweep_gb300_f64_readflush.jsonl.gz")
 DEFAULT_CALIB = os.path.join(PKG, "data", "convert_calib_gb300_f64.jsonl.gz")
+RETIMED_F64 = os.path.join(PKG, "data", "heldout_retimed_gb300_f64.jsonl.gz")
+RETIMED_F32 = os.path.join(PKG, "data", "heldout_retimed_gb300_f32.jsonl.gz")
 MAGIC, VERSION = 2302.0, 1.0
 CFG_FIELDS = ("format", "threads_per_block", "threads_per_row", "unroll", "regcap", "carveout",
               "bsr_block", "hyb_ell_width")

@@ -347,7 +347,10 @@ def heldout_eval(args):
     line per matrix."""
     import torch
     from . import selector as S
-    S.load_default_selector()
+    if args.blob:  # this blob for every value type
+        S.load_default_selector(args.blob, lowp_path=None)
+    else:
+        S.load_default_selector()
     timer = Timer(flush=args.flush, stat=args.stat)
     table = {}
     if args.knob_table:
@@ -419,6 +422,8 @@ def main():
     ap.add_argument("--stat", default="median", choices=["median", "trimmed"],
                     help="statistic of the repetitions (trimmed: mean of the middle 60%%)")
     ap.add_argument("--final-reps", type=int, default=21, help="interleaved repetitions of the final re-timing")
+    ap.add_argument("--blob", default=None, help="selector blob judged by --heldout-eval (default: the committed "
+                                                 "blobs for each value type)")
     ap.add_argument("--knob-table", default=None,
                     help="selector report JSON whose knob_table is also evaluated (heldout-eval)")
     args = ap.parse_args()
