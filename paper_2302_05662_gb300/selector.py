@@ -25,17 +25,20 @@ from . import binding as B
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_BLOB = os.path.join(PKG, "selector_gb300.f32")
-# trained on fp32-value sweeps; used for fp32 and bf16 handles when present
+# trained on fp32-value sweeps; used for fp32 handles, and for bf16 handles
+# when no bf16-trained blob is present
 LOWP_BLOB = os.path.join(PKG, "selector_gb300_fp32_values.f32")
+BF16_BLOB = os.path.join(PKG, "selector_gb300_bf16_values.f32")
 # the exhaustive-sweep records the committed fp64 selector was trained on
 # (every label point of the 2000 dataset matrices, L2 flushed by reading,
 # trimmed means), the conversion-time calibration of its cost model, and the
-# GPU-measured held-out judges (sweep --heldout-eval) of the fp64 and fp32
-# selectors
+# GPU-measured held-out judges (sweep --heldout-eval) of the fp64, fp32 and
+# bf16 selectors
 DEFAULT_DATA = os.path.join(PKG, "data", "sweep_gb300_f64_readflush.jsonl.gz")
 DEFAULT_CALIB = os.path.join(PKG, "data", "convert_calib_gb300_f64.jsonl.gz")
 RETIMED_F64 = os.path.join(PKG, "data", "heldout_retimed_gb300_f64.jsonl.gz")
 RETIMED_F32 = os.path.join(PKG, "data", "heldout_retimed_gb300_f32.jsonl.gz")
+RETIMED_BF16 = os.path.join(PKG, "data", "heldout_retimed_gb300_bf16.jsonl.gz")
 MAGIC, VERSION = 2302.0, 1.0
 CFG_FIELDS = ("format", "threads_per_block", "threads_per_row", "unroll", "regcap", "carveout",
               "bsr_block", "hyb_ell_width")
@@ -100,15 +103,18 @@ def parse_blob(blob) -> dict:
     return out
 
 
-def load_default_selector(path: str = DEFAULT_BLOB, lowp_path: str | None = LOWP_BLOB) -> dict:
+def load_default_selector(path: str = DEFAULT_BLOB, lowp_path: str | None = LOWP_BLOB,
+                          bf16_path: str | None = BF16_BLOB) -> dict:
     """Load the committed trained selector onto the current device (for every
-    value type), and the one trained on fp32 values, if present, for fp32
-    and bf16 handles."""
+    value type), then the ones trained on fp32 and on bf16 values, where
+    present, for handles of those value types (bf16 handles fall back to the
+    fp32-trained blob)."""
     blob = np.fromfile(path, dtype=np.float32)
     B.spmv_selector_load(blob)
     for vt in (B.SPMV_F32, B.SPMV_BF16):
-        if lowp_path and os.path.exists(lowp_path):
-            B.spmv_selector_load_vt(vt, np.fromfile(lowp_path, dtype=np.float32))
+        own = bf16_path if vt == B.SPMV_BF16 and bf16_path and os.path.exists(bf16_path) else lowp_path
+        if own and os.path.exists(own):
+            B.spmv_selector_load_vt(vt, np.fromfile(own, dtype=np.float32))
         else:
             B.spmv_selector_load_vt(vt, None)
     return parse_blob(blob)
@@ -485,18 +491,21 @@ def main():
         W3, b3 = train_time_head(w, X[train_m], T[train_m], D[train_m])
         pack = fit_pack_model([c for c in calib if c["matrix"] < args.holdout_start])
         # time head on held-out matrices: error of the selected class and default CSR
-        lt = predict_logt(w, W3, b3, X[test_m])
-        logits = np.where(np.isfinite(T[test_m]), predict(w, X[test_m]), -np.inf)
-        choice = np.argmax(logits, axis=1)
-        rows = np.arange(choice.size)
-        e_sel = np.abs(lt[rows, choice] - np.log(T[test_m][rows, choice]))
-        e_def = np.abs(lt[:, -1] - np.log(D[test_m]))
-        report["time_head_heldout"] = {"median_abs_log_error_selected": float(np.median(e_sel)),
-                                       "median_abs_log_error_default_csr": float(np.median(e_def)),
-                                       "p90_abs_log_error_selected": float(np.quantile(e_sel, 0.9))}
+        if not test_m.any():   # no held-out sweep records (judged by --heldout-retimed instead)
+            test_m = train_m & False
+        lt = predict_logt(w, W3, b3, X[test_m]) if test_m.any() else None
+        if lt is not None:
+            logits = np.where(np.isfinite(T[test_m]), predict(w, X[test_m]), -np.inf)
+            choice = np.argmax(logits, axis=1)
+            rows = np.arange(choice.size)
+            e_sel = np.abs(lt[rows, choice] - np.log(T[test_m][rows, choice]))
+            e_def = np.abs(lt[:, -1] - np.log(D[test_m]))
+            report["time_head_heldout"] = {"median_abs_log_error_selected": float(np.median(e_sel)),
+                                           "median_abs_log_error_default_csr": float(np.median(e_def)),
+                                           "p90_abs_log_error_selected": float(np.quantile(e_sel, 0.9))}
         # conversion-cost model on held-out calibration records
         held = [c for c in calib if c["matrix"] >= args.holdout_start and c["us"] is not None]
-        if held:
+        if held and lt is not None:
             pred = np.array([pack[c["format"]] @ [1.0, c["nnz"], c["m"]] for c in held])
             meas = np.array([c["us"] for c in held])
             ss_res = float(((pred - meas) ** 2).sum())

@@ -348,7 +348,7 @@ def heldout_eval(args):
     import torch
     from . import selector as S
     if args.blob:  # this blob for every value type
-        S.load_default_selector(args.blob, lowp_path=None)
+        S.load_default_selector(args.blob, lowp_path=None, bf16_path=None)
     else:
         S.load_default_selector()
     timer = Timer(flush=args.flush, stat=args.stat)

@@ -80,15 +80,16 @@ def test_committed_gpu_judges_match_their_reports():
     """The held-out judges measured on the GPU (the device selector's pick
     against the refined exhaustive best, both re-timed in one session),
     recomputed from the committed records, equal the committed reports of
-    the fp64 and fp32 selectors, and each pick is a class of the label
-    space."""
+    the fp64, fp32 and bf16 selectors, and each pick is a class of the
+    label space."""
     import json
     import os
     from paper_2302_05662_gb300 import sweep
     keys = {sweep.config_key(c) for c in sweep.label_space(include_sell=True)}
     pkg = os.path.dirname(S.DEFAULT_BLOB)
     for recs, report in ((S.RETIMED_F64, "selector_gb300_report.json"),
-                         (S.RETIMED_F32, "selector_gb300_fp32_values_report.json")):
+                         (S.RETIMED_F32, "selector_gb300_fp32_values_report.json"),
+                         (S.RETIMED_BF16, "selector_gb300_bf16_values_report.json")):
         got = S.evaluate_retimed([recs])
         rep = json.load(open(os.path.join(pkg, report)))["heldout_retimed"]
         assert got["all"] == rep["all"]
