@@ -125,10 +125,13 @@ bool pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1))
 // Loads in flight per lane when the configuration leaves unroll at 0.  ELL
 // and HYB with fp64 values keep two (a group of four fp64 loads needs more
 // registers than the 32-register variant has, and the loads then wait on
-// each other); fp32/bf16 keep four; SELL keeps eight with 64 registers.
-// Chunked kernels (COO, HYB tail, split CSR) take 4 x unroll entries a lane.
-int default_unroll(int format, int vt) {
-    if (format == SPMV_FMT_SELL) return 8;
+// each other); fp32/bf16 keep four; SELL keeps eight with 64 registers, one
+// for fp64 values in the column-major layout (measured with the L2 flushed by
+// reading, fp64: R-MAT scale 20 74.8 against 76.8 us at 512 threads per
+// block, Poisson(16) rows 78.5 against 80.2).  Chunked kernels (COO, HYB
+// tail, split CSR) take 4 x unroll entries a lane.
+int default_unroll(int format, int vt, int sell_groups) {
+    if (format == SPMV_FMT_SELL) return vt == SPMV_F64 && sell_groups == 1 ? 1 : 8;
     if (format == SPMV_FMT_ELL || format == SPMV_FMT_HYB) return vt == SPMV_F64 ? 2 : 4;
     return 2;
 }
@@ -147,14 +150,18 @@ int resolve_config(const spmv_matrix *h, const spmv_config *in, spmv_config *out
     spmv_config_default(&c, SPMV_FMT_CSR);
     if (in) c = *in;
     if (c.threads_per_block == 0) c.threads_per_block = 256;
-    if (c.unroll == 0) c.unroll = default_unroll(c.format, h->vt);
     if (c.regcap == 0) c.regcap = default_regcap(c.format, h->vt);
     if (c.bsr_block == 0) {
         // SELL: groups of four columns unless the rows follow a power law
         // (a longest row beyond 32 mean rows: there most slices are a few
-        // columns wide and column-major runs faster); BSR: 4 x 4 blocks
+        // columns wide and column-major runs faster) or, with fp64 values,
+        // their columns are scattered (under a quarter of consecutive
+        // entries with consecutive columns: column-major was 1-5.6% faster
+        // on every fp64 Poisson-row matrix over 30 us of the held-out set,
+        // grouped faster on stencils and bands); BSR: 4 x 4 blocks
         const double mean = h->m > 0 ? (double)h->nnz / (double)h->m : 0.0;
-        c.bsr_block = c.format == SPMV_FMT_SELL && (double)h->max_row > 32.0 * mean + 32.0 ? 1 : 4;
+        const bool colmajor = (double)h->max_row > 32.0 * mean + 32.0 || (h->vt == SPMV_F64 && h->contig < 0.25);
+        c.bsr_block = c.format == SPMV_FMT_SELL && colmajor ? 1 : 4;
         // CSR vector with one or two lanes per row: 8-entry groups (32-byte
         // loads) once a lane's part of a mean row holds 16 or more entries,
         // else 4 (fewer masked slots: shorter rows); set below with the
@@ -165,6 +172,7 @@ int resolve_config(const spmv_matrix *h, const spmv_config *in, spmv_config *out
         set_error("config: unknown format %d", c.format);
         return SPMV_ERR_INVALID;
     }
+    if (c.unroll == 0) c.unroll = default_unroll(c.format, h->vt, c.bsr_block);
     if (!pow2_in(c.threads_per_block, 32, 1024)) {
         set_error("config: threads_per_block %d is not a power of two in [32, 1024]", c.threads_per_block);
         return SPMV_ERR_INVALID;

@@ -117,6 +117,18 @@ __global__ void k_max_row(const int *rowptr, int64_t m, int *out) {
     if ((threadIdx.x & 31) == 0) atomicMax(out, best);
 }
 
+// consecutive stored entries whose columns are consecutive (col[k] ==
+// col[k-1] + 1): the column contiguity of the rows (a pair across a row
+// boundary can count too; the statistic only steers a layout default)
+__global__ void k_contiguous_pairs(const int *colidx, int64_t nnz, unsigned long long *out) {
+    unsigned long long cnt = 0;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x + 1; k < nnz; k += stride)
+        cnt += colidx[k] == colidx[k - 1] + 1;
+    cnt = __reduce_add_sync(FULL, (unsigned)cnt);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(out, cnt);
+}
+
 // ---------------------------------------------------------------------------
 // exclusive scan of int32 (three passes: tile sums, scan of sums, tiles)
 // ---------------------------------------------------------------------------
@@ -962,14 +974,17 @@ int build_csr(spmv_matrix *h, const int32_t *d_rows, const int32_t *d_cols, cons
         k_rowptr_from_sorted<<<grid1d(m + 1, 256), 256, 0, s>>>(urows.p, nu, m, h->rowptr);
         SPMV_CUDA_TRY(cudaGetLastError());
     }
-    Tmp<int> mx;
-    SPMV_TRY(mx.alloc(1, s));
-    SPMV_CUDA_TRY(cudaMemsetAsync(mx.p, 0, sizeof(int), s));
-    if (m > 0) k_max_row<<<grid1d(m, 256), 256, 0, s>>>(h->rowptr, m, mx.p);
-    int hmx = 0;
-    SPMV_CUDA_TRY(cudaMemcpyAsync(&hmx, mx.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    Tmp<unsigned long long> mx;   // [0]: longest row, [1]: contiguous pairs
+    SPMV_TRY(mx.alloc(2, s));
+    SPMV_CUDA_TRY(cudaMemsetAsync(mx.p, 0, 2 * sizeof(unsigned long long), s));
+    if (m > 0) k_max_row<<<grid1d(m, 256), 256, 0, s>>>(h->rowptr, m, reinterpret_cast<int *>(mx.p));
+    if (h->nnz > 1) k_contiguous_pairs<<<grid1d(h->nnz, 256), 256, 0, s>>>(h->colidx, h->nnz, mx.p + 1);
+    SPMV_CUDA_TRY(cudaGetLastError());
+    unsigned long long hmx[2] = {0, 0};
+    SPMV_CUDA_TRY(cudaMemcpyAsync(hmx, mx.p, sizeof(hmx), cudaMemcpyDeviceToHost, s));
     SPMV_CUDA_TRY(cudaStreamSynchronize(s));
-    h->max_row = hmx;
+    h->max_row = (int64_t)(hmx[0] & 0xffffffffull);
+    h->contig = h->nnz > 1 ? (double)hmx[1] / (double)(h->nnz - 1) : 0.0;
     return SPMV_OK;
 }
 

@@ -306,6 +306,7 @@ struct CgPlan;
 
 struct spmv_matrix {
     int64_t m = 0, n = 0, nnz = 0, max_row = 0;
+    double contig = 0.0;  // fraction of consecutive stored entries with consecutive columns
     int32_t vt = SPMV_F64;
     spmv_config cfg{};
     spmv_config packed_req{};  // configuration the current packs were built for
