@@ -322,7 +322,6 @@ NAMES = ("stencil27_128^3", "poisson16_2^20", "rmat_s20_ef16", "banded_2^20_w32"
 # reports traffic null.
 NCU_TRAFFIC = {
     ("sell", "banded_2^20_w32", "f64"): (835.5e6, "profiles/sell_banded_2p20_w32_f64.md"),
-    ("sell", "rmat_s20_ef16", "f64"): (225.4e6, "profiles/sell_rmat_s20_f64.md"),
     ("csr", "stencil27_128^3", "f64"): (712.0e6, "profiles/csr_vector_stencil27_128_f64.md"),
     ("ell", "banded_2^20_w32", "f64"): (830.7e6, "profiles/ell_banded_2p20_w32_f64.md"),
 }
