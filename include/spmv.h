@@ -117,7 +117,8 @@ typedef enum {
  *                     flight per lane (ELL, SELL, CSR) or items per lane / 4
  *                     (COO, HYB tail, split CSR; at most 16 items).  0 =
  *                     default: ELL and HYB 2 with fp64 values, 4 with
- *                     fp32/bf16; SELL 8; every other format 2.
+ *                     fp32/bf16; SELL 8 (1 with fp64 values in the
+ *                     column-major layout); every other format 2.
  *   regcap            register cap per thread, 32 (the paper's
  *                     maxrregcount knob) or 64 (the ceiling that keeps
  *                     1024-thread blocks launchable); 48 also for ELL, HYB
@@ -131,7 +132,10 @@ typedef enum {
  *                     columns side by side: 16-byte loads) or 1 (column-
  *                     major); 0 = 4 unless the longest row exceeds 32 mean
  *                     rows plus 32 (power-law rows: mostly narrow slices,
- *                     where column-major runs faster), then 1.  CSR with 1
+ *                     where column-major runs faster) or, with fp64 values,
+ *                     fewer than a quarter of consecutive stored entries
+ *                     have consecutive columns (scattered columns), then 1.
+ *                     CSR with 1
  *                     or 2 lanes per row: entries per lane load, 8 (32-byte
  *                     loads) or 4 (16-byte loads); 0 = 8 when a lane's part
  *                     of a mean-length row holds 16 or more entries, else 4
