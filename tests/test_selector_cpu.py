@@ -194,3 +194,24 @@ def test_evaluate_refined_uses_the_refine_session():
     assert np.isclose(r["with_knob_table"]["geomean_slowdown"], np.sqrt(1.0 * 15 / 8))
     assert np.isclose(r["class_only"]["geomean_slowdown"], np.sqrt(10 / 8 * 15 / 8))
     assert r["with_knob_table"]["within_10pct"] == 0.5
+
+
+def test_sweep_statistics_and_label_keys():
+    """The sweep timer's trimmed mean drops the outer fifth on each side
+    (median below five repetitions); a full configuration maps to the key
+    of its label point (threads per row only for CSR and BSR, block size
+    only for BSR), and every label point maps to itself."""
+    from paper_2302_05662_gb300 import sweep
+    assert sweep.summarize([5.0, 1.0, 3.0], "trimmed") == 3.0
+    assert sweep.summarize([1.0, 2.0, 3.0, 4.0, 100.0], "median") == 3.0
+    assert sweep.summarize([1.0, 2.0, 3.0, 4.0, 100.0], "trimmed") == 3.0      # drops 1 and 100
+    assert abs(sweep.summarize([8.83, 10.88, 8.83, 10.88, 8.83, 10.88, 8.83, 10.88, 8.83, 10.88], "trimmed")
+               - 9.855) < 1e-9
+    full = dict(format=5, threads_per_block=64, threads_per_row=1, unroll=8, regcap=64, carveout=-1,
+                bsr_block=1, hyb_ell_width=128)
+    assert sweep.label_key(full) == "format=5,threads_per_block=64"
+    full_bsr = dict(full, format=4, threads_per_row=4, bsr_block=4)
+    assert sweep.label_key(full_bsr) == "bsr_block=4,format=4,threads_per_block=64,threads_per_row=4"
+    for c in sweep.label_space(include_sell=True):
+        d = dict(dict(threads_per_row=0, bsr_block=0), **c)
+        assert sweep.label_key(d) == sweep.config_key(c)
