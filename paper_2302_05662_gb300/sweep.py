@@ -87,8 +87,8 @@ class Timer:
 
     flush="write" zeroes the buffer between repetitions: the dirty lines it
     leaves are written back while the timed product runs, which slowed
-    products of 2 to 30 million nonzeros by 4-19% against flush="read" (the buffer is
-    read, leaving no dirty line) in the same session on GB300.  stat:
+    products of 2 to 30 million nonzeros by 4-19% against flush="read" (the
+    buffer is read, leaving no dirty line) in the same session on GB300.  stat:
     "median" of the repetitions, or "trimmed" (the mean of the middle 60%):
     the event timer of this GPU ticks in steps of about 2.05 us, so the
     median of a 9 us product is always a whole number of ticks, while the
@@ -314,9 +314,10 @@ def label_key(cfg: dict) -> str:
 
 
 def retime(coo, cfgs, timer: Timer, reps: int, value_dtype="f64", seed=0):
-    """Median microseconds of each configuration, one handle per
-    configuration, repetitions interleaved across the configurations (so a
-    drift of the GPU's state during the session affects them alike)."""
+    """Microseconds of each configuration (the timer's statistic of `reps`
+    repetitions), one handle per configuration, repetitions interleaved
+    across the configurations (so a drift of the GPU's state during the
+    session affects them alike)."""
     import torch
     rows, cols, vals = device_matrix(coo, value_dtype)
     xdt = torch.float64 if value_dtype == "f64" else torch.float32
@@ -345,7 +346,6 @@ def heldout_eval(args):
     the pick is measured against the refined exhaustive best's own re-timed
     time rather than the minimum of many noisy timings.  Appends one JSON
     line per matrix."""
-    import torch
     from . import selector as S
     if args.blob:  # this blob for every value type
         S.load_default_selector(args.blob, lowp_path=None, bf16_path=None)
