@@ -32,7 +32,7 @@ BF16_BLOB = os.path.join(PKG, "selector_gb300_bf16_values.f32")
 # the exhaustive-sweep records the committed fp64 selector was trained on
 # (every label point of the 2000 dataset matrices, L2 flushed by reading,
 # trimmed means), the conversion-time calibration of its cost model, and the
-# GPU-measured held-out judges (sweep --heldout-eval) of the fp64, fp32 and
+# GPU-measured held-out evaluations (sweep --heldout-eval) of the fp64, fp32 and
 # bf16 selectors
 DEFAULT_DATA = os.path.join(PKG, "data", "sweep_gb300_f64_readflush.jsonl.gz")
 DEFAULT_CALIB = os.path.join(PKG, "data", "convert_calib_gb300_f64.jsonl.gz")
@@ -400,7 +400,7 @@ def evaluate_refined(choice_keys, ids, refine: dict, T, labels_keys, table: dict
 
 
 def evaluate_retimed(paths) -> dict:
-    """The held-out judge measured on the GPU (sweep --heldout-eval): per
+    """The held-out evaluation measured on the GPU (sweep --heldout-eval): per
     matrix, the device selector's pick and the refined exhaustive best
     (label space, then register cap x unroll x carveout around its winner)
     timed again in one session with interleaved repetitions.  Slowdown =
@@ -452,7 +452,7 @@ def main():
                     help="refine records (sweep --refine-from): evaluate a per-class register cap / unroll / "
                          "carveout table against the refined exhaustive best")
     ap.add_argument("--heldout-retimed", nargs="*", default=None,
-                    help="records of sweep --heldout-eval: the GPU-measured judge of the blob, added to "
+                    help="records of sweep --heldout-eval: the GPU-measured evaluation of the blob, added to "
                          "the report")
     ap.add_argument("--apply-knobs", action="store_true",
                     help="write the per-class knob table into the blob's labels (default: report only)")
@@ -491,7 +491,7 @@ def main():
         W3, b3 = train_time_head(w, X[train_m], T[train_m], D[train_m])
         pack = fit_pack_model([c for c in calib if c["matrix"] < args.holdout_start])
         # time head on held-out matrices: error of the selected class and default CSR
-        if not test_m.any():   # no held-out sweep records (judged by --heldout-retimed instead)
+        if not test_m.any():   # no held-out sweep records (evaluated by --heldout-retimed instead)
             test_m = train_m & False
         lt = predict_logt(w, W3, b3, X[test_m]) if test_m.any() else None
         if lt is not None:

@@ -338,7 +338,7 @@ def retime(coo, cfgs, timer: Timer, reps: int, value_dtype="f64", seed=0):
 
 
 def heldout_eval(args):
-    """The selector's judge on held-out matrices, in one session: the
+    """The selector's evaluation on held-out matrices, in one session: the
     device selector's pick (spmv_select: features and MLP on the GPU), the
     exhaustive search over the label space, the register cap x unroll x
     carveout space around its winner, then the winner, the pick and default
@@ -416,13 +416,13 @@ def main():
                     help="sweep records: time the register cap x unroll x carveout space around each "
                          "matrix's best label configuration instead")
     ap.add_argument("--heldout-eval", action="store_true",
-                    help="judge the committed selector on matrices start..start+count: its device pick "
+                    help="evaluate the committed selector on matrices start..start+count: its device pick "
                          "against the refined exhaustive best, both re-timed in one session")
     ap.add_argument("--flush", default="write", choices=["write", "read"], help="L2 flush between repetitions")
     ap.add_argument("--stat", default="median", choices=["median", "trimmed"],
                     help="statistic of the repetitions (trimmed: mean of the middle 60%%)")
     ap.add_argument("--final-reps", type=int, default=21, help="interleaved repetitions of the final re-timing")
-    ap.add_argument("--blob", default=None, help="selector blob judged by --heldout-eval (default: the committed "
+    ap.add_argument("--blob", default=None, help="selector blob evaluated by --heldout-eval (default: the committed "
                                                  "blobs for each value type)")
     ap.add_argument("--knob-table", default=None,
                     help="selector report JSON whose knob_table is also evaluated (heldout-eval)")

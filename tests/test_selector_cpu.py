@@ -76,8 +76,8 @@ def test_committed_selector_matches_its_report():
     assert p["version"] == 2 and rep["pack_model_heldout"]["r2"] > 0.9
 
 
-def test_committed_gpu_judges_match_their_reports():
-    """The held-out judges measured on the GPU (the device selector's pick
+def test_committed_gpu_evaluations_match_their_reports():
+    """The held-out evaluations measured on the GPU (the device selector's pick
     against the refined exhaustive best, both re-timed in one session),
     recomputed from the committed records, equal the committed reports of
     the fp64, fp32 and bf16 selectors, and each pick is a class of the
