@@ -324,6 +324,8 @@ NCU_TRAFFIC = {
     ("sell", "banded_2^20_w32", "f64"): (835.5e6, "profiles/sell_banded_2p20_w32_f64.md"),
     ("csr", "stencil27_128^3", "f64"): (712.0e6, "profiles/csr_vector_stencil27_128_f64.md"),
     ("ell", "banded_2^20_w32", "f64"): (830.7e6, "profiles/ell_banded_2p20_w32_f64.md"),
+    ("sell", "rmat_s20_ef16", "f64"): (224.96e6, "profiles/sell_rmat_s20_f64_colmajor_u1.md"),
+    ("sell", "poisson16_2^20", "f64"): (218.24e6, "profiles/sell_poisson16_2p20_f64_colmajor_u1.md"),
 }
 FMT_KEYS = {0: "csr", 1: "ell", 2: "coo", 3: "hyb", 4: "bsr", 5: "sell"}
 
