@@ -123,6 +123,40 @@ def test_select_returns_label_and_falls_back():
         B.spmv_selector_unload()
 
 
+def test_committed_blobs_serve_their_value_types():
+    """load_default_selector: fp64 handles take the fp64-trained blob, fp32
+    handles the fp32-trained one and bf16 handles the bf16-trained one --
+    each device pick is the label the oracle's forward pass of that blob
+    gives on the device features (where the decision is not within fp32
+    rounding of a tie)."""
+    S.load_default_selector()
+    checked = 0
+    try:
+        for vt, path in ((B.SPMV_F64, S.DEFAULT_BLOB), (B.SPMV_F32, S.LOWP_BLOB), (B.SPMV_BF16, S.BF16_BLOB)):
+            p = S.parse_blob(np.fromfile(path, dtype=np.float32))
+            w = {k: p[k].astype(np.float64) for k in ("mu", "sigma", "W1", "b1", "W2", "b2")}
+            for _, coo in CASES[:8]:
+                h = create(coo, vt)
+                try:
+                    cfg, f = B.spmv_select(h)
+                finally:
+                    B.spmv_destroy(h)
+                want = O.mlp_forward(f, w["mu"], w["sigma"], w["W1"], w["b1"], w["W2"], w["b2"])
+                scale = max(1.0, float(np.max(np.abs(want))))
+                top = np.sort(want)[-2:]
+                if top[1] - top[0] <= 1e-3 * scale:
+                    continue
+                lab = dict(zip(S.CFG_FIELDS, p["labels"][int(np.argmax(want))].tolist()))
+                assert (cfg.format, cfg.threads_per_block, cfg.threads_per_row) == \
+                    (lab["format"], lab["threads_per_block"], lab["threads_per_row"]), (vt, lab)
+                checked += 1
+    finally:
+        for vt in (B.SPMV_F32, B.SPMV_BF16):
+            B.spmv_selector_load_vt(vt, None)
+        B.spmv_selector_unload()
+    assert checked >= 12
+
+
 def _fixed_choice_blob(k, label, seed=2):
     w, labels = _random_selector(seed=seed)
     w["W2"][:] = 0.0
