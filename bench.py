@@ -72,6 +72,8 @@ def parse():
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--batched-only", type=int, default=None, metavar="COUNT",
                    help="profiling runs: only the batched section, over COUNT matrices, then exit")
+    p.add_argument("--halo", action="store_true",
+                   help="--mode shard: each rank receives only the window of x its rows touch (one all-to-all)")
     p.add_argument("--mode", default="replicas", choices=["replicas", "shard"],
                    help="N > 1: independent replicas of the step (weak scaling), or every product sharded "
                         "by nnz-balanced row blocks with an all-gather of x (strong scaling)")
@@ -909,7 +911,7 @@ def shard_bench(args, world, rank, local):
         S.load_default_selector()
     xdt = torch.float64 if args.dtype == "f64" else torch.float32
     only = set(args.only.split(",")) if args.only else None
-    mats, flops = [], 0
+    mats, flops, exchanged = [], 0, 0
     for k, (mname, coo) in enumerate(matgen.workload_matrices(args.scale, only=only)):
         rp = np.zeros(coo.m + 1, np.int64)
         np.cumsum(np.bincount(coo.rows, minlength=coo.m), out=rp[1:])
@@ -918,7 +920,8 @@ def shard_bench(args, world, rank, local):
         lr, lc, lv = shard.local_triplets(coo.rows, coo.cols, coo.vals, r0, r1)
         sub = matgen.Coo(r1 - r0, coo.n, lr.astype(np.int32), lc, lv)
         rows, cols, vals = sweep.device_matrix(sub, args.dtype)
-        sm = shard.ShardedMatrix(coo.m, coo.n, rows + r0, cols, vals, bounds, rank, world)
+        sm = shard.ShardedMatrix(coo.m, coo.n, rows + r0, cols, vals, bounds, rank, world, halo=args.halo)
+        exchanged += sm.exchanged_entries()
         del rows, cols, vals
         cfg, _ = B.spmv_select(sm.h)
         B.spmv_set_config(sm.h, cfg)
@@ -952,6 +955,8 @@ def shard_bench(args, world, rank, local):
     if rank == 0:
         cfgd = workload_config(args)
         cfgd["parallelism"] = f"rowshard{world}"
+        cfgd["x_exchange"] = "halo all-to-all" if args.halo else "all-gather"
+        cfgd["x_entries_received_per_step_rank0"] = exchanged
         print(json.dumps({"metric": "SpMV GFLOP/s (row-block sharded product, 5 format-sweep matrices)",
                           "value": round(value, 2), "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
                           "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
