@@ -64,3 +64,21 @@ def test_batched_workload_families_sizes_and_seeds():
         assert coo.name == f"batch{i}_{matgen.FAMILIES[i % 5]}"
         assert 500 <= coo.m <= 300_000 and coo.nnz > 0 and _sorted_unique(coo)
     assert len(list(itertools.islice(matgen.batched_workload(count=3), 10))) == 3
+
+
+def test_column_contiguity_separates_scattered_from_banded_families():
+    """The fp64 SELL layout default takes column-major when fewer than a
+    quarter of consecutive stored entries have consecutive columns: on the
+    generated families that threshold puts Poisson rows and R-MAT below and
+    every stencil (5-, 7-, 27-point), band and block-diagonal above."""
+    def contig(coo):
+        o = np.lexsort((coo.cols, coo.rows))
+        c = coo.cols[o].astype(np.int64)
+        return float(np.mean(c[1:] == c[:-1] + 1))
+    for fam in matgen.FAMILIES:
+        for seed in range(4):
+            f = contig(matgen.family_matrix(fam, 20000, seed=seed, jitter=True))
+            if fam in ("poisson", "rmat"):
+                assert f < 0.2, (fam, seed, f)
+            else:
+                assert f > 0.27, (fam, seed, f)
